@@ -1,0 +1,257 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+
+This module holds no lattice-Boltzmann arithmetic. It only defines
+  * a counter-based random generator (SplitMix64, Steele, Lea & Flood, OOPSLA 2014),
+  * the lattice sizes, relaxation times and face kinds of each workload,
+  * the prescribed boundary-velocity tables of each workload (uniform vectors and
+    parabolic profiles evaluated at node positions),
+  * the request stream of the serving workload.
+
+Face numbering: 0: x=0, 1: x=nx-1, 2: y=0, 3: y=ny-1, 4: z=0, 5: z=nz-1. A velocity
+face carries a float64 table of shape (n2, n1, 3) over its two tangential axes in
+increasing axis order (x faces: [z][y], y faces: [z][x], z faces: [y][x]).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+PERIODIC = 0
+VELOCITY = 1
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 finaliser of a uint64 counter array (wrapping arithmetic)."""
+    with np.errstate(over="ignore"):
+        z = (np.asarray(x, np.uint64) + np.uint64(0x9E3779B97F4A7C15))
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform(seed: int, stream: int, idx) -> np.ndarray:
+    """Uniform [0, 1) doubles at counter positions ``idx`` of (seed, stream)."""
+    idx = np.asarray(idx, np.uint64)
+    with np.errstate(over="ignore"):
+        key = splitmix64(np.uint64(seed) * np.uint64(0x100000001B3) + np.uint64(stream))
+        bits = splitmix64(idx ^ key)
+    return (bits >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def face_shape(face: int, nx: int, ny: int, nz: int) -> tuple[int, int]:
+    """(n2, n1) of the velocity table of a face."""
+    dims = (nx, ny, nz)
+    a = face // 2
+    t1, t2 = [b for b in range(3) if b != a]
+    return dims[t2], dims[t1]
+
+
+def uniform_table(face: int, nx: int, ny: int, nz: int, u) -> np.ndarray:
+    n2, n1 = face_shape(face, nx, ny, nz)
+    t = np.empty((n2, n1, 3))
+    t[...] = np.asarray(u, np.float64)
+    return t
+
+
+def parabola(n: int) -> np.ndarray:
+    """Profile 4 s (n-1-s) / (n-1)^2 on nodes s = 0..n-1: 0 on both end nodes, 1 at
+    the centre of an odd count."""
+    s = np.arange(n, dtype=np.float64)
+    return 4.0 * s * (n - 1 - s) / float((n - 1) ** 2)
+
+
+@dataclass
+class Workload:
+    """One lattice solve: sizes, relaxation time, face kinds and velocity tables."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    tau: float
+    kinds: tuple
+    utabs: list
+    rho0: float = 1.0
+    steps: int = 0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def dims(self):
+        return self.nx, self.ny, self.nz
+
+
+def make_workload(name, nx, ny, nz, tau, face_u, steps=0, rho0=1.0, meta=None) -> Workload:
+    """``face_u[i]`` is None (periodic), a 3-vector (uniform) or a (n2, n1, 3) table."""
+    kinds, tabs = [], []
+    for i in range(6):
+        fu = face_u[i]
+        if fu is None:
+            kinds.append(PERIODIC)
+            tabs.append(None)
+            continue
+        kinds.append(VELOCITY)
+        arr = np.asarray(fu, np.float64)
+        if arr.shape == (3,):
+            arr = uniform_table(i, nx, ny, nz, arr)
+        if arr.shape != face_shape(i, nx, ny, nz) + (3,):
+            raise ValueError(f"face {i}: table shape {arr.shape}")
+        tabs.append(np.ascontiguousarray(arr))
+    return Workload(name, nx, ny, nz, tau, tuple(kinds), tabs, rho0, steps, meta or {})
+
+
+ZERO = (0.0, 0.0, 0.0)
+
+
+def couette(nx=8, ny=8, nz=17, tau=1.0, u_top=0.05, steps=5000) -> Workload:
+    """Shear flow: x, y periodic; wall at z=0 at rest, wall at z=nz-1 moving with
+    (u_top, 0, 0)."""
+    return make_workload("couette", nx, ny, nz, tau,
+                         [None, None, None, None, ZERO, (u_top, 0.0, 0.0)], steps,
+                         meta={"u_top": u_top})
+
+
+def duct(nx=256, ny=64, nz=64, tau=0.6, peak=0.05, angle_deg=30.0, steps=20000) -> Workload:
+    """Square duct: velocity inlet at x=0 with a product-parabola profile of the given
+    peak, tilted by ``angle_deg`` from the x axis in the x-y plane; the same profile
+    prescribed at the outlet x=nx-1; resting walls on the y and z faces."""
+    a = math.radians(angle_deg)
+    prof = peak * np.outer(parabola(nz), parabola(ny))            # [z][y]
+    tab = np.stack([prof * math.cos(a), prof * math.sin(a), np.zeros_like(prof)], axis=-1)
+    return make_workload("duct", nx, ny, nz, tau, [tab, tab, ZERO, ZERO, ZERO, ZERO], steps,
+                         meta={"peak": peak, "angle_deg": angle_deg})
+
+
+def channel(nx=512, ny=512, nz=512, tau=0.8, u=(0.04, 0.01, 0.0), steps=1000) -> Workload:
+    """Channel: uniform velocity u at the inlet x=0 and the outlet x=nx-1, periodic in
+    y, resting walls at z=0 and z=nz-1."""
+    return make_workload("channel", nx, ny, nz, tau, [u, u, None, None, ZERO, ZERO], steps,
+                         meta={"u": tuple(u)})
+
+
+def poiseuille(lz=32, tau=1.0, peak=0.02, lx=4, ly=4, steps=0) -> Workload:
+    """Plane channel between resting walls at z=0 and z=lz-1, periodic in y, with the
+    parabolic profile peak*phi(z) x-hat prescribed at the inlet x=0 and outlet x=lx-1."""
+    prof = peak * np.repeat(parabola(lz)[:, None], ly, axis=1)   # [z][y]
+    tab = np.stack([prof, np.zeros_like(prof), np.zeros_like(prof)], axis=-1)
+    return make_workload("poiseuille", lx, ly, lz, tau, [tab, tab, None, None, ZERO, ZERO], steps,
+                         meta={"peak": peak})
+
+
+def random_face_workload(seed: int, nx: int, ny: int, nz: int, tau: float, periodic=(False, False, False),
+                         amp: float = 0.05) -> Workload:
+    """Random velocity tables on every walled face (for boundary-rule checks)."""
+    face_u = []
+    for i in range(6):
+        if periodic[i // 2]:
+            face_u.append(None)
+            continue
+        n2, n1 = face_shape(i, nx, ny, nz)
+        r = uniform(seed, 100 + i, np.arange(n2 * n1 * 3)).reshape(n2, n1, 3)
+        face_u.append(amp * (2.0 * r - 1.0))
+    return make_workload(f"random{seed}", nx, ny, nz, tau, face_u)
+
+
+# ------------------------------------------------------------------------------------
+# Random perturbation fields for non-equilibrium test states.
+# ------------------------------------------------------------------------------------
+
+def noise(seed: int, shape, stream: int = 0) -> np.ndarray:
+    """Uniform [-1, 1) doubles of a given shape (counter = flat index)."""
+    n = int(np.prod(shape))
+    return (2.0 * uniform(seed, stream, np.arange(n, dtype=np.uint64)) - 1.0).reshape(shape)
+
+
+def noise_at(seed: int, shape, flat_idx, stream: int = 0) -> np.ndarray:
+    """Values of ``noise(seed, shape, stream)`` at flat indices, without building it."""
+    del shape
+    return 2.0 * uniform(seed, stream, np.asarray(flat_idx, np.uint64)) - 1.0
+
+
+def separable_noise_tables(seed: int, nx: int, ny: int, nz: int, q: int = 19, period: int = 61):
+    """Small random tables whose broadcast sum gives a cheap large-lattice field:
+    eps[k,z,y,x] = (a[k,x] + b[k,y] + c[k,z] + d[k,(7x+13y+29z) mod period]) / 4."""
+    a = noise(seed, (q, nx), 1)
+    b = noise(seed, (q, ny), 2)
+    c = noise(seed, (q, nz), 3)
+    d = noise(seed, (q, period), 4)
+    return a, b, c, d
+
+
+def separable_noise_at(tables, nx: int, ny: int, nz: int, flat_idx, q: int = 19, period: int = 61):
+    a, b, c, d = tables
+    flat_idx = np.asarray(flat_idx, np.int64)
+    n = nx * ny * nz
+    k = flat_idx // n
+    node = flat_idx % n
+    x = node % nx
+    y = (node // nx) % ny
+    z = node // (nx * ny)
+    h = (7 * x + 13 * y + 29 * z) % period
+    return (a[k, x] + b[k, y] + c[k, z] + d[k, h]) / 4.0
+
+
+def separable_noise_slab(tables, nx: int, ny: int, z0: int, z1: int, q: int = 19, period: int = 61,
+                         dtype=np.float64) -> np.ndarray:
+    """The field for planes z0..z1-1 as an array (q, z1-z0, ny, nx)."""
+    a, b, c, d = tables
+    zs = np.arange(z0, z1)
+    ys = np.arange(ny)
+    xs = np.arange(nx)
+    h = (7 * xs[None, None, :] + 13 * ys[None, :, None] + 29 * zs[:, None, None]) % period
+    out = (a[:, None, None, :] + b[:, None, :, None] + c[:, zs][:, :, None, None] + d[:, h]) / 4.0
+    return out.astype(dtype, copy=False)
+
+
+# ------------------------------------------------------------------------------------
+# Serving workload: a seeded stream of duct / channel solves.
+# ------------------------------------------------------------------------------------
+
+@dataclass
+class Request:
+    rid: int
+    arrival_s: float
+    kind: str
+    nx: int
+    ny: int
+    nz: int
+    speed: float
+    angle_deg: float
+    tau: float
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+def serving_requests(n: int, seed: int, rate_hz: float, dmin: int = 32, dmax: int = 192):
+    """n requests with Poisson arrivals at ``rate_hz``; dims log-uniform on
+    [dmin, dmax] per axis; speed U(0.01, 0.08); direction angle U(0, 45) degrees in
+    the x-y plane; tau U(0.55, 1.5); kind duct or channel with equal odds."""
+    k = np.arange(n, dtype=np.uint64)
+    u = [uniform(seed, 1000 + j, k) for j in range(8)]
+    gaps = -np.log1p(-u[0]) / rate_hz
+    t = np.cumsum(gaps)
+    lo, hi = math.log(dmin), math.log(dmax)
+    dims = [np.floor(np.exp(lo + (hi - lo) * u[1 + j])).astype(int) for j in range(3)]
+    out = []
+    for i in range(n):
+        out.append(Request(i, float(t[i]), "duct" if u[4][i] < 0.5 else "channel",
+                           int(dims[0][i]), int(dims[1][i]), int(dims[2][i]),
+                           0.01 + 0.07 * float(u[5][i]), 45.0 * float(u[6][i]),
+                           0.55 + 0.95 * float(u[7][i])))
+    return out
+
+
+def request_workload(r: Request) -> Workload:
+    """The lattice solve a serving request asks for."""
+    if r.kind == "duct":
+        return duct(r.nx, r.ny, r.nz, r.tau, r.speed, r.angle_deg, steps=0)
+    a = math.radians(r.angle_deg)
+    return channel(r.nx, r.ny, r.nz, r.tau, (r.speed * math.cos(a), r.speed * math.sin(a), 0.0), steps=0)

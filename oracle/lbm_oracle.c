@@ -1,0 +1,597 @@
+/*
+ * lbm_oracle.c -- plain FP64 CPU oracle for the D3Q19 BGK lattice Boltzmann method
+ * with the on-site velocity boundary condition of Hecht & Harting, "Implementation
+ * of on-site velocity boundary conditions for D3Q19 lattice Boltzmann"
+ * (arXiv:0811.4593).
+ *
+ * TEST INFRASTRUCTURE. This is the slow, obviously-correct statement of what the
+ * CUDA library computes. It shares no code, header or table with that library and
+ * the library never calls it; only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load it.
+ *
+ * Conventions
+ *   - population f_i (i = 1..19, the paper's numbering) lives at array index i-1;
+ *     the F(i) macro below reads and writes it by the paper's index;
+ *   - lattice arrays are [19][nz][ny][nx] with x fastest;
+ *   - faces: 0: x=0, 1: x=nx-1, 2: y=0, 3: y=ny-1, 4: z=0, 5: z=nz-1; a face's
+ *     inward normal is +e_a for the low face and -e_a for the high face of axis a;
+ *   - a velocity face carries a table of prescribed velocities [n2][n1][3], where
+ *     (t1, t2) are the two tangential axes in increasing axis order;
+ *   - an axis is periodic when both of its faces are periodic (kind 0), otherwise
+ *     both of its faces carry the velocity condition (kind 1); v = 0 is no-slip;
+ *   - every sum over populations runs in index order i = 1..19.
+ *
+ * Readings of the paper where it is ambiguous or garbled (all other steps follow the
+ * equations cited at each function):
+ *   R1 Sec. "General on-site velocity boundary condition", eq. bbshort: the compact
+ *      rule prints the coefficient rho/6 for every population; the explicit
+ *      per-plane formulas (eq. f5: rho v_z / 3 for the normal population) require
+ *      6 w_i, i.e. rho/3 for axis and rho/6 for diagonal populations. Used here.
+ *   R2 Sec. "On-site no-slip boundary condition", eq. edge: taken literally, adding
+ *      N c_i.t_i doubles the slip along the edge. The sign that removes it is used:
+ *      f_i = f_-i - (c_i.e) (f_{+e} - f_{-e}) / 4 for every unknown, non-buried i,
+ *      where e is the edge direction.
+ *   R3 eq. buried: the sum runs over the 16 moving populations that are not the two
+ *      buried links (6 axis + 10 diagonal, total weight 22/36), after bounce-back.
+ *   R4 eq. corner: the sum runs over the 12 moving populations with
+ *      c_i.(n1+n2+n3) != 0 (6 axis + 6 diagonal, total weight 18/36).
+ *   R5 edges and corners always take v = 0 (the no-slip rule "can be used on all
+ *      edges" when the in/outflow profile decays to zero there).
+ *   R6 a time step is: pull streaming, boundary closure on the unknown populations,
+ *      then BGK collision; the initial state counts as post-collision.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define Q 19
+
+/* Lattice vectors: c_i is the i-th column of the matrix M (eq. deffs). */
+static const int CV[Q][3] = {
+    {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1}, /* c1..c6 */
+    {1, 1, 0},  {1, -1, 0}, {1, 0, 1},  {1, 0, -1},                         /* c7..c10 */
+    {-1, 1, 0}, {-1, -1, 0}, {-1, 0, 1}, {-1, 0, -1},                       /* c11..c14 */
+    {0, 1, 1},  {0, 1, -1}, {0, -1, 1}, {0, -1, -1},                        /* c15..c18 */
+    {0, 0, 0}};                                                             /* c19 */
+
+/* Lattice weights (eq. weights). */
+static const double WT[Q] = {2.0 / 36, 2.0 / 36, 2.0 / 36, 2.0 / 36, 2.0 / 36, 2.0 / 36,
+                             1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36,
+                             1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36,
+                             12.0 / 36};
+
+#define F(i) f[(i)-1]
+
+enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_UNFILLED = 2 };
+
+static int dot_ci(int k, const int n[3]) { return CV[k][0] * n[0] + CV[k][1] * n[1] + CV[k][2] * n[2]; }
+static double dot_cv(int k, const double v[3]) { return CV[k][0] * v[0] + CV[k][1] * v[1] + CV[k][2] * v[2]; }
+
+/* Index of the population with c = -c_k, found by search. */
+static int opposite(int k) {
+  for (int m = 0; m < Q; ++m)
+    if (CV[m][0] == -CV[k][0] && CV[m][1] == -CV[k][1] && CV[m][2] == -CV[k][2]) return m;
+  return -1;
+}
+
+/* Inward normal of face 0..5. */
+static void face_normal(int face, int n[3]) {
+  n[0] = n[1] = n[2] = 0;
+  n[face / 2] = (face % 2 == 0) ? 1 : -1;
+}
+
+/* ----------------------------------------------------------------------------------
+ * Equilibrium and moments.
+ * -------------------------------------------------------------------------------- */
+
+/* Second-order equilibrium (eq. feq) with c_s^2 = 1/3. */
+void orc_feq(double rho, const double* v, double* feq) {
+  const double cs2 = 1.0 / 3.0;
+  double vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  for (int k = 0; k < Q; ++k) {
+    double cv = dot_cv(k, v);
+    feq[k] = WT[k] * rho * (1.0 + cv / cs2 + cv * cv / (2.0 * cs2 * cs2) - vv / (2.0 * cs2));
+  }
+}
+
+/* Density (eq. rho) and velocity (eq. vel); out = {rho, v_x, v_y, v_z}. */
+void orc_moments(const double* f, double* out) {
+  double rho = 0, j[3] = {0, 0, 0};
+  for (int k = 0; k < Q; ++k) {
+    rho += f[k];
+    for (int a = 0; a < 3; ++a) j[a] += f[k] * CV[k][a];
+  }
+  out[0] = rho;
+  for (int a = 0; a < 3; ++a) out[a + 1] = j[a] / rho;
+}
+
+/* BGK collision (eq. bgk): f <- f - (f - f_eq(rho, v)) / tau. */
+void orc_collide(double* f, double tau) {
+  double m[4], feq[Q];
+  orc_moments(f, m);
+  orc_feq(m[0], m + 1, feq);
+  for (int k = 0; k < Q; ++k) f[k] = f[k] - (f[k] - feq[k]) / tau;
+}
+
+/* ----------------------------------------------------------------------------------
+ * Face closure, form (i): the explicit per-plane formulas. Each returns rho and
+ * overwrites the five unknown populations; v is the prescribed velocity in lattice
+ * axes.
+ * -------------------------------------------------------------------------------- */
+
+/* Bottom plane z = 0: eq. uin, eq. f5, eq. f9-f17, eq. Nx, eq. Ny. */
+static double close_bottom(double* f, const double* v) {
+  double rho = (F(1) + F(2) + F(3) + F(4) + F(7) + F(8) + F(11) + F(12) + F(19) +
+                2.0 * (F(6) + F(10) + F(14) + F(16) + F(18))) / (1.0 - v[2]);
+  double Nx = 0.5 * (F(1) + F(7) + F(8) - (F(2) + F(11) + F(12))) - rho * v[0] / 3.0;
+  double Ny = 0.5 * (F(3) + F(7) + F(11) - (F(4) + F(8) + F(12))) - rho * v[1] / 3.0;
+  F(5) = F(6) + rho * v[2] / 3.0;
+  F(9) = F(14) + rho / 6.0 * (v[2] + v[0]) - Nx;
+  F(13) = F(10) + rho / 6.0 * (v[2] - v[0]) + Nx;
+  F(15) = F(18) + rho / 6.0 * (v[2] + v[1]) - Ny;
+  F(17) = F(16) + rho / 6.0 * (v[2] - v[1]) + Ny;
+  return rho;
+}
+
+/* Top plane z = nz-1: appendix, top plane. */
+static double close_top(double* f, const double* v) {
+  double rho = (F(1) + F(2) + F(3) + F(4) + F(7) + F(11) + F(12) + F(8) + F(19) +
+                2.0 * (F(5) + F(9) + F(13) + F(15) + F(17))) / (v[2] + 1.0);
+  double Nx = 0.5 * (F(1) + F(7) + F(8) - (F(2) + F(11) + F(12))) - rho * v[0] / 3.0;
+  double Ny = 0.5 * (F(3) + F(7) + F(11) - (F(4) + F(8) + F(12))) - rho * v[1] / 3.0;
+  F(6) = F(5) - rho * v[2] / 3.0;
+  F(10) = F(13) + rho / 6.0 * (-v[2] + v[0]) - Nx;
+  F(14) = F(9) + rho / 6.0 * (-v[2] - v[0]) + Nx;
+  F(16) = F(17) + rho / 6.0 * (-v[2] + v[1]) - Ny;
+  F(18) = F(15) + rho / 6.0 * (-v[2] - v[1]) + Ny;
+  return rho;
+}
+
+/* Left plane x = 0: appendix, eq. rhooutx, eq. Nxy, eq. Nxz. */
+static double close_left(double* f, const double* v) {
+  double rho = (F(3) + F(4) + F(5) + F(6) + F(15) + F(16) + F(17) + F(18) + F(19) +
+                2.0 * (F(2) + F(11) + F(12) + F(13) + F(14))) / (1.0 - v[0]);
+  double Ny = 0.5 * (F(3) + F(15) + F(16) - (F(4) + F(17) + F(18))) - rho * v[1] / 3.0;
+  double Nz = 0.5 * (F(5) + F(17) + F(15) - (F(6) + F(16) + F(18))) - rho * v[2] / 3.0;
+  F(1) = F(2) + rho * v[0] / 3.0;
+  F(8) = F(11) + rho / 6.0 * (v[0] - v[1]) + Ny;
+  F(7) = F(12) + rho / 6.0 * (v[0] + v[1]) - Ny;
+  F(9) = F(14) + rho / 6.0 * (v[0] + v[2]) - Nz;
+  F(10) = F(13) + rho / 6.0 * (v[0] - v[2]) + Nz;
+  return rho;
+}
+
+/* Right plane x = nx-1: appendix, eq. rhoinx. */
+static double close_right(double* f, const double* v) {
+  double rho = (F(3) + F(4) + F(5) + F(6) + F(15) + F(16) + F(17) + F(18) + F(19) +
+                2.0 * (F(1) + F(7) + F(8) + F(9) + F(10))) / (v[0] + 1.0);
+  double Ny = 0.5 * (F(3) + F(15) + F(16) - (F(4) + F(17) + F(18))) - rho * v[1] / 3.0;
+  double Nz = 0.5 * (F(5) + F(17) + F(15) - (F(6) + F(16) + F(18))) - rho * v[2] / 3.0;
+  F(2) = F(1) - rho * v[0] / 3.0;
+  F(11) = F(8) + rho / 6.0 * (-v[0] + v[1]) - Ny;
+  F(12) = F(7) + rho / 6.0 * (-v[0] - v[1]) + Ny;
+  F(14) = F(9) + rho / 6.0 * (-v[0] - v[2]) + Nz;
+  F(13) = F(10) + rho / 6.0 * (-v[0] + v[2]) - Nz;
+  return rho;
+}
+
+/* Front plane y = 0: appendix, eq. rhoiny, eq. Nyx, eq. Nyz. */
+static double close_front(double* f, const double* v) {
+  double rho = (F(1) + F(2) + F(5) + F(6) + F(9) + F(10) + F(13) + F(14) + F(19) +
+                2.0 * (F(4) + F(8) + F(12) + F(17) + F(18))) / (1.0 - v[1]);
+  double Nx = 0.5 * (F(1) + F(9) + F(10) - (F(2) + F(13) + F(14))) - rho * v[0] / 3.0;
+  double Nz = 0.5 * (F(5) + F(9) + F(13) - (F(6) + F(10) + F(14))) - rho * v[2] / 3.0;
+  F(3) = F(4) + rho * v[1] / 3.0;
+  F(7) = F(12) + rho / 6.0 * (v[1] + v[0]) - Nx;
+  F(11) = F(8) + rho / 6.0 * (v[1] - v[0]) + Nx;
+  F(15) = F(18) + rho / 6.0 * (v[1] + v[2]) - Nz;
+  F(16) = F(17) + rho / 6.0 * (v[1] - v[2]) + Nz;
+  return rho;
+}
+
+/* Back plane y = ny-1: appendix, eq. rhoouty (velocity form; the printed v_x of the
+ * density-given variant is read as v_y, which this velocity form does not use). */
+static double close_back(double* f, const double* v) {
+  double rho = (F(1) + F(2) + F(5) + F(6) + F(9) + F(10) + F(13) + F(14) + F(19) +
+                2.0 * (F(3) + F(7) + F(11) + F(15) + F(16))) / (v[1] + 1.0);
+  double Nx = 0.5 * (F(1) + F(9) + F(10) - (F(2) + F(13) + F(14))) - rho * v[0] / 3.0;
+  double Nz = 0.5 * (F(5) + F(9) + F(13) - (F(6) + F(10) + F(14))) - rho * v[2] / 3.0;
+  F(4) = F(3) - rho * v[1] / 3.0;
+  F(12) = F(7) + rho / 6.0 * (-v[1] - v[0]) + Nx;
+  F(8) = F(11) + rho / 6.0 * (-v[1] + v[0]) - Nx;
+  F(18) = F(15) + rho / 6.0 * (-v[1] - v[2]) + Nz;
+  F(17) = F(16) + rho / 6.0 * (-v[1] + v[2]) - Nz;
+  return rho;
+}
+
+/* ----------------------------------------------------------------------------------
+ * Face closure, form (ii): the compact rule for any plane (eq. bbshort, reading R1).
+ * For every population i pointing out of the domain (c_i.n < 0) the population -i
+ * pointing in is
+ *   f_-i = f_i - 6 w_i rho c_i.v - (rho/3) t_i.v + 1/2 sum_j f_j (t_i.c_j)(1 - |c_j.n|)
+ * with t_i = c_i - (c_i.n) n and rho from the plane's density relation (eq. uin).
+ * -------------------------------------------------------------------------------- */
+static double close_face_compact(double* f, int face, const double* v) {
+  int n[3];
+  face_normal(face, n);
+  /* density: in-plane populations once, outgoing ones twice, unknown ones not at all */
+  double s = 0.0;
+  for (int k = 0; k < Q; ++k) {
+    int cn = dot_ci(k, n);
+    if (cn == 0) s += f[k];
+    else if (cn < 0) s += 2.0 * f[k];
+  }
+  double vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+  double rho = s / (1.0 - vn);
+  for (int k = 0; k < Q; ++k) {
+    int cn = dot_ci(k, n);
+    if (cn >= 0) continue; /* only outgoing i */
+    double t[3];
+    for (int a = 0; a < 3; ++a) t[a] = CV[k][a] - cn * n[a];
+    double tv = t[0] * v[0] + t[1] * v[1] + t[2] * v[2];
+    double corr = 0.0; /* sum over in-plane j; the factor (1-|c_j.n|) drops the rest */
+    for (int j = 0; j < Q; ++j) {
+      if (dot_ci(j, n) != 0) continue;
+      double tc = t[0] * CV[j][0] + t[1] * CV[j][1] + t[2] * CV[j][2];
+      corr += f[j] * tc;
+    }
+    f[opposite(k)] = f[k] - 6.0 * WT[k] * rho * dot_cv(k, v) - rho / 3.0 * tv + 0.5 * corr;
+  }
+  return rho;
+}
+
+/* Entry for both forms: form 0 = explicit per-plane formulas, form 1 = compact rule. */
+int orc_close_face(int face, int form, double* f, const double* v, double* rho_out) {
+  double rho;
+  if (face < 0 || face > 5) return ORC_ERR_ARG;
+  if (form == 1) {
+    rho = close_face_compact(f, face, v);
+  } else {
+    switch (face) {
+      case 0: rho = close_left(f, v); break;
+      case 1: rho = close_right(f, v); break;
+      case 2: rho = close_front(f, v); break;
+      case 3: rho = close_back(f, v); break;
+      case 4: rho = close_bottom(f, v); break;
+      default: rho = close_top(f, v); break;
+    }
+  }
+  if (rho_out) *rho_out = rho;
+  return ORC_OK;
+}
+
+/* ----------------------------------------------------------------------------------
+ * Concave edge, no-slip (Sec. "On-site no-slip boundary condition", eq. Nxzy,
+ * eq. edge, eq. buried; readings R2, R3). n1, n2 are the inward normals of the
+ * two planes meeting at the edge.
+ * -------------------------------------------------------------------------------- */
+static void close_edge_normals(double* f, const int n1[3], const int n2[3]) {
+  int e[3] = {n1[1] * n2[2] - n1[2] * n2[1], n1[2] * n2[0] - n1[0] * n2[2],
+              n1[0] * n2[1] - n1[1] * n2[0]};
+  int buried[Q], unknown[Q];
+  for (int k = 0; k < Q; ++k) {
+    int d = 1, m = 1;
+    for (int a = 0; a < 3; ++a) {
+      if (CV[k][a] != n1[a] - n2[a]) d = 0;
+      if (CV[k][a] != n2[a] - n1[a]) m = 0;
+    }
+    buried[k] = d || m;
+    unknown[k] = dot_ci(k, n1) > 0 || dot_ci(k, n2) > 0;
+  }
+  /* 1. bounce back every unknown population that is not a buried link */
+  for (int k = 0; k < Q; ++k)
+    if (unknown[k] && !buried[k]) f[k] = f[opposite(k)];
+  /* 2. remove the momentum left along the edge: N = 1/4 sum_j f_j (c_j.e) over the
+   *    populations lying in both planes (eq. Nxzy, eq. edge) */
+  double Ne = 0.0;
+  for (int j = 0; j < Q; ++j) {
+    if (dot_ci(j, n1) != 0 || dot_ci(j, n2) != 0) continue;
+    Ne += f[j] * dot_ci(j, e);
+  }
+  Ne *= 0.25;
+  for (int k = 0; k < Q; ++k)
+    if (unknown[k] && !buried[k]) f[k] -= dot_ci(k, e) * Ne;
+  /* 3. buried links and rest population (eq. buried) */
+  double s = 0.0;
+  for (int k = 0; k < Q - 1; ++k)
+    if (!buried[k]) s += f[k];
+  double fb = s / 22.0;
+  for (int k = 0; k < Q - 1; ++k)
+    if (buried[k]) f[k] = fb;
+  F(19) = 12.0 * fb;
+}
+
+int orc_close_edge(int face_a, int face_b, double* f) {
+  if (face_a < 0 || face_a > 5 || face_b < 0 || face_b > 5 || face_a / 2 == face_b / 2) return ORC_ERR_ARG;
+  int n1[3], n2[3];
+  face_normal(face_a, n1);
+  face_normal(face_b, n2);
+  close_edge_normals(f, n1, n2);
+  return ORC_OK;
+}
+
+/* ----------------------------------------------------------------------------------
+ * Corner, no-slip (eq. corner, reading R4).
+ * -------------------------------------------------------------------------------- */
+static void close_corner_normals(double* f, const int n1[3], const int n2[3], const int n3[3]) {
+  int s3[3] = {n1[0] + n2[0] + n3[0], n1[1] + n2[1] + n3[1], n1[2] + n2[2] + n3[2]};
+  int buried[Q], unknown[Q];
+  for (int k = 0; k < Q; ++k) {
+    buried[k] = (k < Q - 1) && dot_ci(k, s3) == 0;
+    unknown[k] = dot_ci(k, n1) > 0 || dot_ci(k, n2) > 0 || dot_ci(k, n3) > 0;
+  }
+  for (int k = 0; k < Q; ++k)
+    if (unknown[k] && !buried[k]) f[k] = f[opposite(k)];
+  double s = 0.0;
+  for (int k = 0; k < Q - 1; ++k)
+    if (!buried[k]) s += f[k];
+  double fb = s / 18.0;
+  for (int k = 0; k < Q - 1; ++k)
+    if (buried[k]) f[k] = fb;
+  F(19) = 12.0 * fb;
+}
+
+int orc_close_corner(int face_x, int face_y, int face_z, double* f) {
+  if (face_x < 0 || face_x > 1 || face_y < 2 || face_y > 3 || face_z < 4 || face_z > 5) return ORC_ERR_ARG;
+  int n1[3], n2[3], n3[3];
+  face_normal(face_x, n1);
+  face_normal(face_y, n2);
+  face_normal(face_z, n3);
+  close_corner_normals(f, n1, n2, n3);
+  return ORC_OK;
+}
+
+/* ----------------------------------------------------------------------------------
+ * Lattice: streaming, classification, one time step.
+ * -------------------------------------------------------------------------------- */
+typedef struct {
+  int nx, ny, nz;
+  int kind[6];            /* 0 periodic, 1 velocity */
+  const double* utab[6];  /* [n2][n1][3] per velocity face */
+  double tau;
+} lattice_t;
+
+static int axis_dim(const lattice_t* L, int a) { return a == 0 ? L->nx : (a == 1 ? L->ny : L->nz); }
+static int axis_periodic(const lattice_t* L, int a) { return L->kind[2 * a] == 0; }
+
+static int lattice_check(const lattice_t* L) {
+  if (L->nx < 1 || L->ny < 1 || L->nz < 1) return ORC_ERR_ARG;
+  for (int a = 0; a < 3; ++a) {
+    if (L->kind[2 * a] != L->kind[2 * a + 1]) return ORC_ERR_ARG; /* periodic faces come in pairs */
+    if (L->kind[2 * a] != 0 && L->kind[2 * a] != 1) return ORC_ERR_ARG;
+    if (L->kind[2 * a] == 1 && axis_dim(L, a) < 3) return ORC_ERR_ARG;
+    if (L->kind[2 * a] == 1 && (!L->utab[2 * a] || !L->utab[2 * a + 1])) return ORC_ERR_ARG;
+  }
+  return ORC_OK;
+}
+
+/* Linear index of the node that population k at (x,y,z) is pulled from, i.e.
+ * x - c_k (streaming step, with wrap-around on periodic axes), or -1 when that node
+ * lies outside the domain (the population is unknown after streaming). */
+static int64_t pull_source(const lattice_t* L, int x, int y, int z, int k) {
+  int p[3] = {x - CV[k][0], y - CV[k][1], z - CV[k][2]};
+  for (int a = 0; a < 3; ++a) {
+    int n = axis_dim(L, a);
+    if (p[a] < 0 || p[a] >= n) {
+      if (!axis_periodic(L, a)) return -1;
+      p[a] = ((p[a] % n) + n) % n;
+    }
+  }
+  return ((int64_t)p[2] * L->ny + p[1]) * L->nx + p[0];
+}
+
+/* Prescribed velocity at (x,y,z) on face `face` (tangential axes in increasing order). */
+static const double* face_velocity(const lattice_t* L, int face, int x, int y, int z) {
+  int c[3] = {x, y, z};
+  int a = face / 2, t1 = (a == 0) ? 1 : 0, t2 = (a == 2) ? 1 : 2;
+  int n1 = axis_dim(L, t1);
+  return L->utab[face] + 3 * ((int64_t)c[t2] * n1 + c[t1]);
+}
+
+/* Boundary closure and collision of one node whose streamed populations are in f
+ * (NaN marks an unknown population). */
+static int update_node(const lattice_t* L, int x, int y, int z, double* f, int form) {
+  int c[3] = {x, y, z};
+  int faces[3], nf = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (axis_periodic(L, a)) continue;
+    if (c[a] == 0) faces[nf++] = 2 * a;
+    else if (c[a] == axis_dim(L, a) - 1) faces[nf++] = 2 * a + 1;
+  }
+  if (nf == 1) {
+    orc_close_face(faces[0], form, f, face_velocity(L, faces[0], x, y, z), NULL);
+  } else if (nf == 2) {
+    int n1[3], n2[3];
+    face_normal(faces[0], n1);
+    face_normal(faces[1], n2);
+    close_edge_normals(f, n1, n2);
+  } else if (nf == 3) {
+    int n1[3], n2[3], n3[3];
+    face_normal(faces[0], n1);
+    face_normal(faces[1], n2);
+    face_normal(faces[2], n3);
+    close_corner_normals(f, n1, n2, n3);
+  }
+  for (int k = 0; k < Q; ++k)
+    if (isnan(f[k])) return ORC_ERR_UNFILLED;
+  orc_collide(f, L->tau);
+  return ORC_OK;
+}
+
+static int make_lattice(lattice_t* L, int nx, int ny, int nz, const int* kind,
+                        const double* const* utab, double tau) {
+  L->nx = nx; L->ny = ny; L->nz = nz; L->tau = tau;
+  for (int i = 0; i < 6; ++i) {
+    L->kind[i] = kind[i];
+    L->utab[i] = utab ? utab[i] : NULL;
+  }
+  return lattice_check(L);
+}
+
+/* Pull streaming only: out[k][node] = in[k][node - c_k], NaN where unknown. */
+int orc_stream(int nx, int ny, int nz, const int* kind, const double* fin, double* fout) {
+  lattice_t L;
+  const double* none[6] = {0, 0, 0, 0, 0, 0};
+  double dummy = 0.0;
+  for (int i = 0; i < 6; ++i) none[i] = &dummy; /* tables unused by streaming */
+  int rc = make_lattice(&L, nx, ny, nz, kind, none, 1.0);
+  if (rc) return rc;
+  int64_t N = (int64_t)nx * ny * nz;
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        int64_t node = ((int64_t)z * ny + y) * nx + x;
+        for (int k = 0; k < Q; ++k) {
+          int64_t s = pull_source(&L, x, y, z, k);
+          fout[k * N + node] = (s < 0) ? NAN : fin[k * N + s];
+        }
+      }
+  return ORC_OK;
+}
+
+/* One time step fin -> fout (streaming, closure, collision). */
+int orc_step(int nx, int ny, int nz, const int* kind, const double* const* utab, double tau,
+             const double* fin, double* fout, int form) {
+  lattice_t L;
+  int rc = make_lattice(&L, nx, ny, nz, kind, utab, tau);
+  if (rc) return rc;
+  int64_t N = (int64_t)nx * ny * nz;
+  int err = 0;
+#pragma omp parallel for schedule(static) reduction(| : err)
+  for (int z = 0; z < nz; ++z) {
+    double f[Q];
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        int64_t node = ((int64_t)z * ny + y) * nx + x;
+        for (int k = 0; k < Q; ++k) {
+          int64_t s = pull_source(&L, x, y, z, k);
+          f[k] = (s < 0) ? NAN : fin[k * N + s];
+        }
+        err |= update_node(&L, x, y, z, f, form);
+        for (int k = 0; k < Q; ++k) fout[k * N + node] = f[k];
+      }
+  }
+  return err;
+}
+
+/* nsteps time steps; f holds the initial and the final state, work is scratch of the
+ * same size. */
+int orc_run(int nx, int ny, int nz, const int* kind, const double* const* utab, double tau,
+            int nsteps, double* f, double* work, int form) {
+  int64_t n = (int64_t)Q * nx * ny * nz;
+  double *a = f, *b = work;
+  for (int s = 0; s < nsteps; ++s) {
+    int rc = orc_step(nx, ny, nz, kind, utab, tau, a, b, form);
+    if (rc) return rc;
+    double* t = a; a = b; b = t;
+  }
+  if (a != f) memcpy(f, a, (size_t)n * sizeof(double));
+  return ORC_OK;
+}
+
+/* f = f_eq(rho0, 0) on every node (the initial, post-collision state). */
+void orc_init_equilibrium(int nx, int ny, int nz, double rho0, double* f) {
+  int64_t N = (int64_t)nx * ny * nz;
+  double v0[3] = {0, 0, 0}, feq[Q];
+  orc_feq(rho0, v0, feq);
+  for (int k = 0; k < Q; ++k)
+    for (int64_t i = 0; i < N; ++i) f[k * N + i] = feq[k];
+}
+
+/* Density [nz][ny][nx] and velocity [3][nz][ny][nx] of a stored state. */
+void orc_macros(int nx, int ny, int nz, const double* f, double* rho, double* u) {
+  int64_t N = (int64_t)nx * ny * nz;
+  for (int64_t i = 0; i < N; ++i) {
+    double g[Q], m[4];
+    for (int k = 0; k < Q; ++k) g[k] = f[k * N + i];
+    orc_moments(g, m);
+    rho[i] = m[0];
+    for (int a = 0; a < 3; ++a) u[a * N + i] = m[a + 1];
+  }
+}
+
+/* Reductions in node order: out = {sum rho, sum |u - u_prev|^2, sum |u|^2,
+ * number of nodes with a non-finite or non-positive density or velocity}.
+ * u_prev may be NULL (taken as zero). */
+void orc_reduce(int nx, int ny, int nz, const double* f, const double* u_prev, double* out) {
+  int64_t N = (int64_t)nx * ny * nz;
+  double mass = 0, du2 = 0, u2 = 0, bad = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    double g[Q], m[4];
+    for (int k = 0; k < Q; ++k) g[k] = f[k * N + i];
+    orc_moments(g, m);
+    int ok = isfinite(m[0]) && m[0] > 0;
+    for (int a = 0; a < 3; ++a) {
+      double up = u_prev ? u_prev[a * N + i] : 0.0;
+      du2 += (m[a + 1] - up) * (m[a + 1] - up);
+      u2 += m[a + 1] * m[a + 1];
+      ok = ok && isfinite(m[a + 1]);
+    }
+    mass += m[0];
+    bad += ok ? 0 : 1;
+  }
+  out[0] = mass; out[1] = du2; out[2] = u2; out[3] = bad;
+}
+
+/* Pull sources of a list of nodes: src[i*19 + k] = k*N + (node - c_k) or -1. */
+int orc_sources(int nx, int ny, int nz, const int* kind, int64_t n, const int64_t* nodes, int64_t* src) {
+  lattice_t L;
+  double dummy = 0.0;
+  const double* none[6] = {&dummy, &dummy, &dummy, &dummy, &dummy, &dummy};
+  int rc = make_lattice(&L, nx, ny, nz, kind, none, 1.0);
+  if (rc) return rc;
+  int64_t N = (int64_t)nx * ny * nz;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t node = nodes[i];
+    if (node < 0 || node >= N) return ORC_ERR_ARG;
+    int x = (int)(node % nx), y = (int)((node / nx) % ny), z = (int)(node / ((int64_t)nx * ny));
+    for (int k = 0; k < Q; ++k) {
+      int64_t s = pull_source(&L, x, y, z, k);
+      src[i * Q + k] = (s < 0) ? -1 : (int64_t)k * N + s;
+    }
+  }
+  return ORC_OK;
+}
+
+/* Closure and collision of listed nodes from their streamed populations
+ * (g[i*19 + k], NaN where unknown); results in out[i*19 + k]. */
+int orc_update_gathered(int nx, int ny, int nz, const int* kind, const double* const* utab,
+                        double tau, int64_t n, const int64_t* nodes, const double* g,
+                        double* out, int form) {
+  lattice_t L;
+  int rc = make_lattice(&L, nx, ny, nz, kind, utab, tau);
+  if (rc) return rc;
+  int64_t N = (int64_t)nx * ny * nz;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t node = nodes[i];
+    if (node < 0 || node >= N) return ORC_ERR_ARG;
+    int x = (int)(node % nx), y = (int)((node / nx) % ny), z = (int)(node / ((int64_t)nx * ny));
+    double f[Q];
+    for (int k = 0; k < Q; ++k) f[k] = g[i * Q + k];
+    rc = update_node(&L, x, y, z, f, form);
+    if (rc) return rc;
+    for (int k = 0; k < Q; ++k) out[i * Q + k] = f[k];
+  }
+  return ORC_OK;
+}
+
+/* Tables for inspection by the tests: c (19x3), w (19), opposite index (19). */
+void orc_lattice(int* c, double* w, int* opp) {
+  for (int k = 0; k < Q; ++k) {
+    for (int a = 0; a < 3; ++a) c[3 * k + a] = CV[k][a];
+    w[k] = WT[k];
+    opp[k] = opposite(k);
+  }
+}
+
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
