@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fused D3Q19 sweep (MLUPS and HBM-roofline fraction).
+
+Default workload: the 512^3 channel -- tau 0.8, uniform non-normal inflow and outflow
+u = (0.04, 0.01, 0) at x = 0 and x = 511, periodic in y, no-slip walls at z = 0 and
+z = 511 -- with FP32 population storage; 1000 timed steps after 200 warm-up steps and a
+fused residual/mass reduction every 100 steps, as a steady-state solve runs. One time
+step is one pass of the hot path over all 512^3 nodes. The populations (10.2 GB read
+and 10.2 GB written per step) are far larger than the 129 MB L2, so no flush is needed.
+
+Arms:
+  --impl native     the CUDA library through its Python binding (default);
+  --impl reference  the FP64 CPU oracle on the host cores, on a bounded sample of the
+                    same workload (the paper publishes no implementation to run).
+Under torchrun every rank runs an independent replica on its own GPU (the solve has
+no data-path exchange); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lbm_inputs as inp  # noqa: E402
+
+METRIC = "MLUPS & % HBM roofline (FP16/FP32 vs FP64) at stated error; serving p50/p99"
+BYTES_PER_UPDATE = {"f64": 304, "f32": 152, "f16": 76}  # 19 loads + 19 stores per node update
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload(name: str):
+    if name == "channel512":
+        return inp.channel(512, 512, 512, 0.8, (0.04, 0.01, 0.0))
+    if name == "channel256":  # the same channel at 256^3, for profiler captures
+        return inp.channel(256, 256, 256, 0.8, (0.04, 0.01, 0.0))
+    if name == "duct":
+        return inp.duct(256, 64, 64, 0.6, 0.05, 30.0)
+    if name == "couette":
+        return inp.couette()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def describe(wl) -> str:
+    if wl.name == "channel":
+        return (f"channel {wl.nx}x{wl.ny}x{wl.nz}, tau {wl.tau}, uniform inflow/outflow u={wl.meta['u']} at x faces, "
+                f"periodic y, no-slip z walls")
+    if wl.name == "duct":
+        return (f"square duct {wl.nx}x{wl.ny}x{wl.nz}, tau {wl.tau}, parabolic inlet/outlet peak {wl.meta['peak']} "
+                f"tilted {wl.meta['angle_deg']} deg, no-slip y and z walls")
+    return f"{wl.name} {wl.nx}x{wl.ny}x{wl.nz}, tau {wl.tau}"
+
+
+def cpu_sample(wl):
+    """The bounded oracle sample of a workload: same faces, tau and inflow, fewer planes."""
+    if wl.name == "channel":
+        s = inp.channel(128, 128, 16, wl.tau, wl.meta["u"])
+        return s, f"channel {s.nx}x{s.ny}x{s.nz} (same faces, tau and inflow as the workload)"
+    if wl.name == "duct":
+        s = inp.duct(wl.nx, wl.ny, wl.nz, wl.tau, wl.meta["peak"], wl.meta["angle_deg"])
+        return s, "the full duct"
+    return wl, "the full lattice"
+
+
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def sweep_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "d3q19.cuh", "lbm_internal.h"):
+        with open(os.path.join(ROOT, "paper_0811_4593_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, precision: str, wl_name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current sweep source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh)[f"{kernel}/{precision}/{wl_name}"]
+    except Exception:  # noqa: BLE001
+        return None
+    return rec["dram_bytes_per_launch"] if rec.get("source_sha") == sweep_source_hash() else None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------
+# native arm
+# ------------------------------------------------------------------------------------
+
+def timed_steps(lat, steps: int, resid_every: int, events: bool):
+    """Issue `steps` time steps, a fused residual every `resid_every`. Returns per-step
+    CUDA events (on the lattice's stream) and the indices of residual steps."""
+    import torch
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)] if events else None
+    if evs:
+        evs[0].record(lat.stream)
+    resid = []
+    for s in range(steps):
+        if resid_every and (s + 1) % resid_every == 0:
+            lat.step_residual(1)
+            resid.append(s)
+        else:
+            lat.step(1)
+        if evs:
+            evs[s + 1].record(lat.stream)
+    return evs, resid
+
+
+def measure(lat, steps, warmup, resid_every, dist_ctx, clock_gpu=None):
+    import torch
+    timed_steps(lat, warmup, resid_every, events=False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(clock_gpu).start() if clock_gpu is not None else None
+    dist_ctx.barrier()
+    torch.cuda.synchronize()
+    l0 = lat.info()["kernel_launches"]
+    evs, resid = timed_steps(lat, steps, resid_every, events=True)
+    torch.cuda.synchronize()
+    dist_ctx.barrier()
+    clock = clocks.stop() if clocks else None
+    launches = lat.info()["kernel_launches"] - l0
+    total_ms = evs[0].elapsed_time(evs[steps])
+    per = [evs[s].elapsed_time(evs[s + 1]) for s in range(steps)]
+    after_sync = {s + 1 for s in resid}
+    plain = [per[s] for s in range(steps) if s not in resid and s not in after_sync]
+    return total_ms, (sum(plain) / len(plain) if plain else total_ms / steps), launches, clock
+
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = False
+
+    def init(self):
+        import torch
+        torch.cuda.set_device(self.local)
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            self.pg = True
+
+    def barrier(self):
+        if self.pg:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+def run_variant(wl, precision, steps, warmup, resid_every, dist_ctx):
+    import paper_0811_4593_gb300 as lbm
+    with lbm.Lattice.from_workload(wl, precision) as lat:
+        total_ms, step_ms, launches, _ = measure(lat, steps, warmup, resid_every, dist_ctx)
+    hbm, _ = measured_hbm_peak()
+    ach = BYTES_PER_UPDATE[precision] * wl.cells / (step_ms * 1e-3) / 1e9
+    return {"mlups": wl.cells * steps / (total_ms * 1e-3) / 1e6, "ms_per_step": total_ms / steps,
+            "sweep_ms": step_ms, "achieved_gbs": ach, "frac": ach / hbm, "steps": steps,
+            "bytes_per_update": BYTES_PER_UPDATE[precision]}
+
+
+def e2e_run(wl, precision, steps, resid_every, dist_ctx):
+    """Same solve through the public API with host buffers: upload the initial
+    populations from pinned host memory, run the steps, read the density and velocity
+    fields back to pinned host memory -- all inside the timed region."""
+    import torch
+
+    import paper_0811_4593_gb300 as lbm
+    with lbm.Lattice.from_workload(wl, precision) as lat:
+        dt = {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16}[precision]
+        mdt = torch.float64 if precision == "f64" else torch.float32
+        f_host = torch.empty((19, wl.nz, wl.ny, wl.nx), dtype=dt, pin_memory=True)
+        lat.get_populations(out=f_host)          # the initial state, staged on the host
+        rho_dev = torch.empty((wl.nz, wl.ny, wl.nx), dtype=mdt, device="cuda")
+        u_dev = torch.empty((3, wl.nz, wl.ny, wl.nx), dtype=mdt, device="cuda")
+        rho_host = torch.empty(rho_dev.shape, dtype=mdt, pin_memory=True)
+        u_host = torch.empty(u_dev.shape, dtype=mdt, pin_memory=True)
+        torch.cuda.synchronize()
+        dist_ctx.barrier()
+        t0 = time.perf_counter()
+        lat.set_populations(f_host)
+        timed_steps(lat, steps, resid_every, events=False)
+        lat.macros(rho_dev, u_dev)
+        rho_host.copy_(rho_dev, non_blocking=True)
+        u_host.copy_(u_dev, non_blocking=True)
+        torch.cuda.synchronize()
+        dt_s = time.perf_counter() - t0
+        dist_ctx.barrier()
+        h2d = f_host.numel() * f_host.element_size()
+        d2h = rho_host.numel() * rho_host.element_size() + u_host.numel() * u_host.element_size() + \
+            32 * (steps // resid_every if resid_every else 0)
+    return dt_s, h2d, d2h
+
+
+def cpu_baseline(wl, seconds: float):
+    import oracle
+    sample, text = cpu_sample(wl)
+    olat = oracle.Lattice.from_workload(sample)
+    f = oracle.init_equilibrium(olat, sample.rho0)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        f = oracle.step(olat, f)
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": sample.cells * n / dt / 1e6, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{text}, {n} FP64 steps from rest in {dt:.1f} s"}
+
+
+def native(args):
+    import torch
+
+    import paper_0811_4593_gb300 as lbm
+    from paper_0811_4593_gb300 import build as lib_build
+    d = Dist()
+    if d.rank == 0 or not os.path.exists(lib_build.LIB):
+        lib_build.build()
+    d.init()
+    wl = workload(args.workload)
+    hbm, hbm_src = measured_hbm_peak()
+    with lbm.Lattice.from_workload(wl, args.precision) as lat:
+        total_ms, sweep_ms, launches, clock = measure(lat, args.steps, args.warmup, args.resid_every, d,
+                                                      clock_gpu=d.local)
+    total_ms = d.max(total_ms)
+    sweep_ms = d.max(sweep_ms)
+    value = d.world * wl.cells * args.steps / (total_ms * 1e-3) / 1e6
+    achieved = BYTES_PER_UPDATE[args.precision] * wl.cells / (sweep_ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": d.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": describe(wl), "nodes": wl.cells, "precision": f"{args.precision} population storage",
+                   "residual_every": args.resid_every, "parallelism": "replicas" if d.world > 1 else "single GPU",
+                   "l2": f"inputs larger than L2: {BYTES_PER_UPDATE[args.precision] * wl.cells / 2e9:.1f} GB of "
+                         f"populations read per step (no flush needed)"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "peak_source": hbm_src,
+                     "traffic": profiled_traffic("sweep", args.precision, args.workload),
+                     "kernel": f"sweep_kernel<{args.precision}>",
+                     "bytes_per_update": BYTES_PER_UPDATE[args.precision], "updates_per_launch": wl.cells,
+                     "sweep_ms": round(sweep_ms, 4)},
+        "gpu_launches": launches,
+        "clocks": clock,
+    }
+    if not args.no_e2e:
+        dt_s, h2d, d2h = e2e_run(wl, args.precision, args.steps, args.resid_every, d)
+        dt_s = d.max(dt_s)
+        out["e2e"] = {"value": round(d.world * wl.cells * args.steps / dt_s / 1e6, 1), "unit": "MLUPS",
+                      "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+    if d.world == 1 and not args.no_variants and args.workload == "channel512":
+        torch.cuda.empty_cache()
+        vs = {}
+        for p in ("f16", "f64"):
+            if p != args.precision:
+                vs[p] = run_variant(wl, p, args.variant_steps, 20, args.resid_every, d)
+                torch.cuda.empty_cache()
+        out["variants"] = vs
+    if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    d.close()
+    if d.rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def reference(args):
+    """The FP64 oracle on the host cores, `--steps` timed steps after `--warmup` on the
+    bounded sample of the workload; rank 0 only."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    import oracle
+    wl = workload(args.workload)
+    sample, text = cpu_sample(wl)
+    olat = oracle.Lattice.from_workload(sample)
+    f = oracle.init_equilibrium(olat, sample.rho0)
+    f = oracle.run(olat, f, args.warmup)
+    t0 = time.perf_counter()
+    f = oracle.run(olat, f, args.steps)
+    dt = time.perf_counter() - t0
+    value = sample.cells * args.steps / dt / 1e6
+    out = {"metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": describe(wl), "nodes": wl.cells, "precision": "f64 (oracle)",
+                      "parallelism": "host cores"},
+           "cpu_baseline": {"value": round(value, 2), "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
+                            "sample": f"{text}, {args.steps} FP64 steps after {args.warmup} warm-up steps"},
+           "e2e": {"value": round(value, 2), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default="channel512", choices=["channel512", "channel256", "duct", "couette"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f16", "f64"])
+    ap.add_argument("--resid-every", type=int, default=100)
+    ap.add_argument("--variant-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference(args)
+    else:
+        native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * lbm.h -- C ABI of the GB300 D3Q19 lattice Boltzmann library (liblbm.so).
+ *
+ * The library advances a D3Q19 BGK lattice with the on-site velocity boundary
+ * condition of Hecht & Harting, "Implementation of on-site velocity boundary
+ * conditions for D3Q19 lattice Boltzmann" (arXiv:0811.4593), on one CUDA device.
+ * One time step is one fused CUDA sweep: pull streaming, the boundary closure on
+ * the populations left unknown by streaming, then BGK collision.
+ *
+ * Conventions used throughout
+ *  - Lattice vectors c_1..c_19 are the columns of the paper's matrix M (eq. deffs);
+ *    population i is stored at index i-1. Weights follow eq. weights.
+ *  - Population arrays are structure-of-arrays [19][nz][ny][nx], x fastest, in the
+ *    storage type of the context's precision (see lbm_precision).
+ *  - Faces: 0: x=0, 1: x=nx-1, 2: y=0, 3: y=ny-1, 4: z=0, 5: z=nz-1. The inward
+ *    normal of face 2a is +e_a, of face 2a+1 it is -e_a.
+ *  - Every function returns an lbm_status; no C++ exception crosses the ABI. On an
+ *    error, lbm_last_error() describes it.
+ *  - A context belongs to the CUDA device that was current at lbm_create; every
+ *    call makes that device current. A context is not thread-safe.
+ *  - Work is issued asynchronously on the context's stream (lbm_set_stream) unless a
+ *    function says it synchronises.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque; created and owned by the library */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,      /* invalid argument or unsupported boundary specification */
+  LBM_ERR_OOM = -2,      /* the allocator returned NULL */
+  LBM_ERR_CUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+  LBM_ERR_DIVERGED = -4, /* a reduction found a non-finite or non-positive density or
+                            a non-finite velocity */
+  LBM_ERR_STATE = -5     /* call not valid in the context's current state */
+} lbm_status;
+
+/* Storage of the populations and the arithmetic of the sweep.
+ *  LBM_F64          f_i stored as double; all arithmetic in double.
+ *  LBM_F32          f_i stored as float; arithmetic in float except the density of a
+ *                   face closure (eq. uin and its appendix analogues), which is formed
+ *                   in double, and the reductions, which accumulate in double.
+ *  LBM_F16_SHIFTED  h_i = f_i - w_i rho0 stored as IEEE binary16 (round to nearest
+ *                   even); arithmetic as for LBM_F32. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16_SHIFTED = 2 } lbm_precision;
+
+/* Periodic faces wrap streaming to the opposite face (periodic boundaries of the
+ * paper's Sec. "Boundary conditions") and must come in pairs. A velocity face applies
+ * the on-site velocity condition; a prescribed velocity of zero is the on-site
+ * no-slip wall (Sec. "On-site no-slip boundary condition"). */
+typedef enum { LBM_FACE_PERIODIC = 0, LBM_FACE_VELOCITY = 1 } lbm_face_kind;
+
+typedef enum { LBM_HOST = 0, LBM_DEVICE = 1 } lbm_memory;
+
+typedef struct {
+  int kind;              /* lbm_face_kind */
+  double u[3];           /* prescribed velocity (lattice units) on every node of the face,
+                            used when u_table is NULL */
+  const double* u_table; /* optional HOST array [n2][n1][3] of prescribed velocities, one
+                            per node of the face plane, over the face's two tangential
+                            axes in increasing axis order (x faces [z][y], y faces [z][x],
+                            z faces [y][x]); copied by lbm_create, not retained */
+} lbm_face_spec;
+
+/* Device allocator hook: every device buffer the library owns is obtained through
+ * alloc(bytes, user) and returned through release(ptr, user). Default: cudaMalloc and
+ * cudaFree. Takes effect for allocations made after the call; release is always
+ * called with the hook that allocated the pointer. NULL alloc restores the default. */
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* user);
+typedef void (*lbm_free_fn)(void* ptr, void* user);
+LBM_API lbm_status lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void* user);
+
+/* Create a lattice of nx x ny x nz nodes.
+ *  tau   BGK relaxation time (eq. bgk); kinematic viscosity (tau - 1/2)/3 (eq. visc).
+ *  faces six face descriptions (see lbm_face_spec).
+ *  rho0  initial density; the initial state is the post-collision state
+ *        f_i = f_i^eq(rho0, 0) (eq. feq).
+ * Validation (LBM_ERR_ARG): tau > 1/2; every dimension >= 3; 19 * nx*ny*nz < 2^32;
+ * periodic faces in pairs; |u.n| < 1 on every velocity face node. On edges and
+ * corners (nodes on two or three velocity faces) the no-slip rules of Sec. "On-site
+ * no-slip boundary condition" apply and the face tables are not read there.
+ * Ownership: *out is owned by the library until lbm_destroy. */
+LBM_API lbm_status lbm_create(int nx, int ny, int nz, double tau, const lbm_face_spec faces[6],
+                      lbm_precision prec, double rho0, lbm_ctx** out);
+
+/* Release every device buffer of the context (after synchronising its stream) and the
+ * context itself. NULL is accepted. */
+LBM_API lbm_status lbm_destroy(lbm_ctx* ctx);
+
+/* Use `cuda_stream` (a cudaStream_t; NULL = legacy default stream) for all later work
+ * of the context. */
+LBM_API lbm_status lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
+
+/* Advance n >= 0 time steps, asynchronously. Each step is, per node: pull streaming
+ * f_i(x) = f*_i(x - c_i) with wrap-around on periodic axes (Sec. "Simulation method",
+ * Sec. "Boundary conditions"); on face nodes the density relation eq. uin and the
+ * unknown populations eq. f5, eqs. f9-f17 with the corrections eqs. Nx, Ny (and their
+ * appendix analogues for the other planes); on edge and corner nodes bounce-back with
+ * the edge correction eq. edge, buried links eq. buried and eq. corner; then BGK
+ * collision (eq. bgk, eq. feq). */
+LBM_API lbm_status lbm_step(lbm_ctx* ctx, int n);
+
+/* Advance n >= 1 steps like lbm_step, the last one also forming, in double, the
+ * total mass sum(rho) and the steady-state residual
+ *   r = sqrt(sum |u - u_snap|^2) / sqrt(sum |u|^2)
+ * where u_snap is the velocity field at the previous residual evaluation (zero
+ * before the first one); u_snap is then replaced by the current field. Synchronises.
+ * Returns LBM_ERR_DIVERGED (after writing *residual and *mass) when any node has a
+ * non-finite or non-positive density or a non-finite velocity. The residual is not
+ * part of the paper; it is the library's steady-state criterion. */
+LBM_API lbm_status lbm_step_residual(lbm_ctx* ctx, int n, double* residual, double* mass);
+
+/* Same reductions as lbm_step_residual, evaluated on the stored post-collision state
+ * without advancing it (density and velocity are collision invariants, so this is the
+ * state after the last step's closure). Synchronises. */
+LBM_API lbm_status lbm_residual(lbm_ctx* ctx, double* residual, double* mass);
+
+/* Density (eq. rho) into rho[nz][ny][nx] and velocity (eq. vel) into u[3][nz][ny][nx]
+ * of the stored state. Both are caller-owned DEVICE buffers of double for LBM_F64,
+ * float otherwise. Asynchronous. Either pointer may be NULL. */
+LBM_API lbm_status lbm_macros(lbm_ctx* ctx, void* rho, void* u);
+
+/* Copy the planes z0 .. z0+nzs-1 of the stored populations from / to a caller buffer
+ * laid out [19][nzs][ny][nx] in the storage type (double, float, or binary16 holding
+ * h_i = f_i - w_i rho0). `where` says whether the caller buffer is host or device
+ * memory. Synchronises. The state written by lbm_set_populations counts as
+ * post-collision. */
+LBM_API lbm_status lbm_set_populations(lbm_ctx* ctx, const void* src, int z0, int nzs, lbm_memory where);
+LBM_API lbm_status lbm_get_populations(lbm_ctx* ctx, void* dst, int z0, int nzs, lbm_memory where);
+
+/* Block the host until the context's stream is idle; reports asynchronous errors. */
+LBM_API lbm_status lbm_sync(lbm_ctx* ctx);
+
+typedef struct {
+  int nx, ny, nz;
+  int precision;            /* lbm_precision */
+  int64_t steps;            /* time steps taken since lbm_create */
+  int64_t kernel_launches;  /* CUDA kernels the context has launched */
+  int64_t bytes_per_update; /* algorithmic bytes moved per node update: 19 loads + 19
+                               stores of the storage type */
+  int64_t device_bytes;     /* device memory the context holds */
+} lbm_info_t;
+LBM_API lbm_status lbm_info(const lbm_ctx* ctx, lbm_info_t* out);
+
+/* Last error message of a context, or of the calling thread's last failed call that
+ * had no context (ctx == NULL). Never NULL. */
+LBM_API const char* lbm_last_error(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,68 @@
+// lbm_internal.h -- interface between the C-ABI runtime (runtime.cu) and the kernel
+// translation units (sweep_f64.cu, sweep_f32.cu, sweep_f16.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cstdint>
+
+namespace lbm {
+
+// Unsigned 32-bit division by an invariant divisor with one multiply-high, after
+// Granlund & Montgomery, "Division by invariant integers using multiplication"
+// (PLDI 1994), Fig. 4.1: q = (t + ((n - t) >> s1)) >> s2 with t = mulhi(m, n).
+struct FastDiv {
+  uint32_t d, m, s1, s2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;  // l = ceil(log2 d)
+  FastDiv f;
+  f.d = d;
+  f.m = uint32_t(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t fdiv(const FastDiv& f, uint32_t n) {
+  uint32_t t = __umulhi(f.m, n);
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+#endif
+
+// Boundary data of one face for the sweep.
+struct FaceBC {
+  const double* tab;  // device [n2][n1][3] or nullptr (uniform u)
+  double u[3];
+};
+
+// Everything one sweep launch needs, passed by value.
+struct SweepArgs {
+  const void* src;   // storage [19][N], post-collision state of the previous step
+  void* dst;         // storage [19][N], post-collision state after this step
+  uint32_t nx, ny, nz, N;
+  FastDiv div_nx, div_ny;
+  uint32_t periodic;  // bit a set: axis a is periodic
+  double rho0;
+  double omega;       // 1 / tau
+  FaceBC face[6];
+  void* snap;         // residual steps: [3][N] velocity snapshot in the compute type
+  double* partials;   // residual steps: [blocks][4] per-block sums
+};
+
+constexpr int SWEEP_THREADS = 256;
+constexpr int REDUCE_THREADS = 1024;
+
+inline uint32_t sweep_blocks(uint32_t N) { return (N + SWEEP_THREADS - 1) / SWEEP_THREADS; }
+
+template <typename S> cudaError_t launch_sweep(const SweepArgs& a, bool resid, cudaStream_t s);
+template <typename S> cudaError_t launch_init(void* dst, uint32_t N, double rho0, cudaStream_t s);
+template <typename S> cudaError_t launch_macros(const void* src, uint32_t N, double rho0, void* rho,
+                                                void* u, cudaStream_t s);
+template <typename S> cudaError_t launch_state_reduce(const void* src, uint32_t N, double rho0,
+                                                      void* snap, double* partials, cudaStream_t s);
+cudaError_t launch_final_reduce(const double* partials, uint32_t nblocks, double* out, cudaStream_t s);
+
+}  // namespace lbm
