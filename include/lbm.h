@@ -51,9 +51,10 @@ typedef enum {
 
 /* Storage of the populations and the arithmetic of the sweep.
  *  LBM_F64          f_i stored as double; all arithmetic in double.
- *  LBM_F32          f_i stored as float; arithmetic in float except the density of a
- *                   face closure (eq. uin and its appendix analogues), which is formed
- *                   in double, and the reductions, which accumulate in double.
+ *  LBM_F32          shifted populations h_i = f_i - w_i rho0 stored as float;
+ *                   arithmetic in float except the density of a face closure (eq. uin
+ *                   and its appendix analogues), which is formed in double, and the
+ *                   reductions, which accumulate in double.
  *  LBM_F16_SHIFTED  h_i = f_i - w_i rho0 stored as IEEE binary16 (round to nearest
  *                   even); arithmetic as for LBM_F32. */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16_SHIFTED = 2 } lbm_precision;
@@ -135,8 +136,8 @@ LBM_API lbm_status lbm_residual(lbm_ctx* ctx, double* residual, double* mass);
 LBM_API lbm_status lbm_macros(lbm_ctx* ctx, void* rho, void* u);
 
 /* Copy the planes z0 .. z0+nzs-1 of the stored populations from / to a caller buffer
- * laid out [19][nzs][ny][nx] in the storage type (double, float, or binary16 holding
- * h_i = f_i - w_i rho0). `where` says whether the caller buffer is host or device
+ * laid out [19][nzs][ny][nx] in the storage type: double holding f_i for LBM_F64,
+ * float or binary16 holding h_i = f_i - w_i rho0 for LBM_F32 and LBM_F16_SHIFTED. `where` says whether the caller buffer is host or device
  * memory. Synchronises. The state written by lbm_set_populations counts as
  * post-collision. */
 LBM_API lbm_status lbm_set_populations(lbm_ctx* ctx, const void* src, int z0, int nzs, lbm_memory where);

@@ -161,7 +161,8 @@ class Lattice:
 
     ``faces`` lists the six faces (x=0, x=nx-1, y=0, y=ny-1, z=0, z=nz-1); each is None
     (periodic), a velocity 3-vector, or a table of prescribed velocities (n2, n1, 3).
-    ``precision`` is "f64", "f32" or "f16" (binary16 storage of f - w rho0).
+    ``precision`` is "f64" (f stored as double), "f32" or "f16" (f - w rho0 stored as
+    float or binary16).
     """
 
     def __init__(self, nx, ny, nz, tau, faces, precision="f32", rho0=1.0, stream=None,
@@ -262,8 +263,8 @@ class Lattice:
 
     def set_populations(self, f, z0: int = 0):
         """Load planes z0.. of the state from an array [19][nzs][ny][nx] in the storage
-        dtype (float16 holds f - w rho0); a numpy array is read from host memory, a
-        CUDA tensor from device memory."""
+        dtype (float64 holds f; float32 and float16 hold f - w rho0); a numpy array is
+        read from host memory, a CUDA tensor from device memory."""
         nzs = int(f.shape[1])
         self._check_pop_shape(f, nzs)
         if isinstance(f, np.ndarray):

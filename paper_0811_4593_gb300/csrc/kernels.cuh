@@ -5,8 +5,9 @@
 // closure and collision rules are linear in f with weights that sum to one where a
 // density is formed, so they hold unchanged for h (sum_i w_i c_i = 0 and the density
 // relation's weights sum to 1); the shift keeps the small deviations from rest at
-// full precision in float arithmetic. FP64 and FP32 storage hold f_i, binary16
-// storage holds h_i.
+// full precision in float arithmetic. FP64 storage holds f_i; FP32 and binary16
+// storage hold h_i, so their rounding is relative to the small deviation from rest
+// rather than to f_i itself.
 #pragma once
 #include <cuda_fp16.h>
 #include <type_traits>
@@ -35,8 +36,8 @@ template <> struct Codec<double> {
   __device__ static double store(double h, double shift) { return h + shift; }
 };
 template <> struct Codec<float> {
-  __device__ static float load(const float* p, float shift) { return __ldg(p) - shift; }
-  __device__ static float store(float h, float shift) { return h + shift; }
+  __device__ static float load(const float* p, float) { return __ldg(p); }
+  __device__ static float store(float h, float) { return h; }
 };
 template <> struct Codec<__half> {
   __device__ static float load(const __half* p, float) { return __half2float(__ldg(p)); }

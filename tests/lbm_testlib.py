@@ -23,18 +23,17 @@ def encode(f, prec, rho0=1.0):
     """FP64 populations -> the storage array of a precision."""
     if prec == "f64":
         return np.ascontiguousarray(f, np.float64)
-    if prec == "f32":
-        return np.ascontiguousarray(f, np.float32)
     w = weights()
-    return np.ascontiguousarray(f - (w * rho0)[:, None, None, None], np.float16)
+    h = f - (w * rho0)[:, None, None, None]
+    return np.ascontiguousarray(h, np.float32 if prec == "f32" else np.float16)
 
 
 def decode(s, prec, rho0=1.0):
     """Storage array -> FP64 populations."""
-    if prec == "f16":
-        w = weights()
-        return s.astype(np.float64) + (w * rho0)[:, None, None, None]
-    return s.astype(np.float64)
+    if prec == "f64":
+        return s.astype(np.float64)
+    w = weights()
+    return s.astype(np.float64) + (w * rho0)[:, None, None, None]
 
 
 def run_pair(wl, prec, f0, steps, form=0):
@@ -86,6 +85,4 @@ def separable_value_at(tables, nx, ny, nz, idx, amp, prec, rho0=1.0):
     f = wr * (1.0 + amp * eps)
     if prec == "f64":
         return f
-    if prec == "f32":
-        return f.astype(np.float32).astype(np.float64)
-    return (f - wr).astype(np.float16).astype(np.float64) + wr
+    return (f - wr).astype(np.float32 if prec == "f32" else np.float16).astype(np.float64) + wr
