@@ -157,6 +157,36 @@ typedef struct {
 } lbm_info_t;
 LBM_API lbm_status lbm_info(const lbm_ctx* ctx, lbm_info_t* out);
 
+/* Reduction of a caller-held population array that allocates nothing (the paper has no
+ * counterpart; it is the state reduction of lbm_residual without a context).
+ *
+ * For callers that cannot call cudaMalloc: code that runs while all device memory is
+ * owned by another pool or framework, code that must not trigger the device-wide
+ * synchronisation cudaMalloc and cudaFree can cause, and code running where new device
+ * allocations are forbidden. Every buffer is the caller's; the only scratch, 2 MiB of
+ * per-block partial sums, is a static array inside the library that every device
+ * which loads the library holds until the process exits.
+ *
+ *  populations        DEVICE [19][nz][ny][nx] in the storage type of `prec` (double f_i
+ *                     for LBM_F64; float / binary16 h_i = f_i - w_i rho0 otherwise)
+ *  velocity_snapshot  DEVICE [3][nz][ny][nx], double for LBM_F64 else float: read as
+ *                     u_snap, then overwritten with the current velocity
+ *  sums               DEVICE double[4], written with {sum rho, sum |u - u_snap|^2,
+ *                     sum |u|^2, number of nodes with a non-finite or non-positive
+ *                     density or a non-finite velocity}; the residual of lbm_residual is
+ *                     sqrt(sums[1]) / sqrt(sums[2])
+ *  cuda_stream        stream for the two kernel launches (NULL = legacy default stream)
+ * Limit: at most 16,777,216 nodes (256^3); larger lattices get LBM_ERR_ARG with a
+ * message naming the limit. Asynchronous; nothing is allocated and nothing is freed.
+ * The first call on a device looks up the static array's device address (with that
+ * device current); make that first call before any stream capture. All calls share
+ * the one array, which keeps the last call's contents (every call overwrites the part
+ * it reads, so nothing needs clearing): calls that overlap on the GPU, e.g. on two
+ * streams at once, race and give wrong sums. */
+LBM_API lbm_status lbm_reduce_state_static(const void* populations, int nx, int ny, int nz,
+                                           lbm_precision prec, double rho0, void* velocity_snapshot,
+                                           double* sums, void* cuda_stream);
+
 /* Last error message of a context, or of the calling thread's last failed call that
  * had no context (ctx == NULL). Never NULL. */
 LBM_API const char* lbm_last_error(const lbm_ctx* ctx);

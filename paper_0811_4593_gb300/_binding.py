@@ -38,6 +38,8 @@ EXPORTS = {
     "lbm_sync": (C.c_int, [C.c_void_p]),
     "lbm_info": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
+    "lbm_reduce_state_static": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p,
+                                          C.c_void_p, C.c_void_p]),
 }
 
 

@@ -65,4 +65,7 @@ template <typename S> cudaError_t launch_state_reduce(const void* src, uint32_t 
                                                       void* snap, double* partials, cudaStream_t s);
 cudaError_t launch_final_reduce(const double* partials, uint32_t nblocks, double* out, cudaStream_t s);
 
+// Sets the calling thread's context-free error message (lbm_last_error(NULL)).
+void record_error(const char* msg);
+
 }  // namespace lbm

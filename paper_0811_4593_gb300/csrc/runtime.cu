@@ -205,6 +205,10 @@ lbm_status finish_reduction(lbm_ctx* ctx, double* residual, double* mass) {
 
 }  // namespace
 
+namespace lbm {
+void record_error(const char* msg) { g_err = msg; }
+}  // namespace lbm
+
 extern "C" {
 
 lbm_status lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void* user) {
