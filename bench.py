@@ -335,6 +335,42 @@ def native(args):
         print(json.dumps(out), flush=True)
 
 
+def serving(args):
+    """The serving mix: capacity (jobs/s) from a closed-loop run of the seed-1 request
+    stream, then the seed-0 stream with Poisson arrivals at 70 % of that capacity."""
+    import torch
+
+    from paper_0811_4593_gb300 import build as lib_build
+    from paper_0811_4593_gb300.serving import Job, Server
+    lib_build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    kw = dict(capacity=args.slots, budget_bytes=args.budget_gb * 1e9, round_steps=args.resid_every,
+              max_steps=args.max_steps, target=args.target, plateau_checks=10)
+    cap_reqs = inp.serving_requests(args.capacity_requests, 1, 1.0)
+    cap_jobs = [Job(r.rid, 0.0, inp.request_workload(r)) for r in cap_reqs]
+    _, cap = Server(args.precision, **kw).serve(cap_jobs, closed_loop=True)
+    capacity = cap["jobs_per_s"]
+    rate = 0.7 * capacity
+    reqs = inp.serving_requests(args.requests, 0, rate)
+    jobs = [Job(r.rid, r.arrival_s, inp.request_workload(r)) for r in reqs]
+    results, rep = Server(args.precision, **kw).serve(jobs)
+    out = {"metric": METRIC, "value": round(rep["aggregate_mlups"], 1), "unit": "MLUPS", "n_gpus": 1,
+           "higher_is_better": True, "dtype": args.precision, "data": "synthetic", "mode": "serving",
+           "config": {"workload": f"serving mix: {args.requests} duct/channel requests, dims log-uniform 32..192, "
+                                  f"speed U(0.01,0.08), angle U(0,45 deg), tau U(0.55,1.5), Poisson arrivals at "
+                                  f"0.7 x capacity, residual target {args.target} or {args.max_steps} steps",
+                      "slots": args.slots, "budget_gb": args.budget_gb, "round_steps": args.resid_every},
+           "serving": {"p50_time_to_steady_s": round(rep["p50_time_to_steady_s"], 3),
+                       "p99_time_to_steady_s": round(rep["p99_time_to_steady_s"], 3),
+                       "jobs": rep["jobs"], "wall_s": round(rep["wall_s"], 2),
+                       "capacity_jobs_per_s": round(capacity, 3), "arrival_rate_per_s": round(rate, 3),
+                       "capacity_run": {"jobs": cap["jobs"], "wall_s": round(cap["wall_s"], 2),
+                                        "aggregate_mlups": round(cap["aggregate_mlups"], 1)},
+                       "status_counts": rep["status_counts"], "peak_active": rep["peak_active"],
+                       "peak_gb": round(rep["peak_bytes"] / 1e9, 2)}}
+    print(json.dumps(out), flush=True)
+
+
 def reference(args):
     """The FP64 oracle on the host cores, `--steps` timed steps after `--warmup` on the
     bounded sample of the workload; rank 0 only."""
@@ -376,11 +412,20 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", action="store_true", help="run the serving mix instead of the sweep benchmark")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--capacity-requests", type=int, default=200)
+    ap.add_argument("--slots", type=int, default=512)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--max-steps", type=int, default=20000)
+    ap.add_argument("--target", type=float, default=1e-8)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         reference(args)
+    elif args.serving:
+        serving(args)
     else:
         native(args)
 

@@ -157,6 +157,69 @@ typedef struct {
 } lbm_info_t;
 LBM_API lbm_status lbm_info(const lbm_ctx* ctx, lbm_info_t* out);
 
+/* ---------------------------------------------------------------------------------
+ * Batches: many resident lattices advanced together (continuous-batching serving).
+ *
+ * A batch advances every attached context by one persistent CUDA launch per time step:
+ * the launch splits the 256-node blocks of all attached lattices into one contiguous
+ * share per thread block and runs, per node, exactly the computation of lbm_step (same
+ * device code, same grouping of the residual sums), so an attached lattice evolves to
+ * the same bits as when it is stepped alone. The n-step loop is captured once as a
+ * CUDA graph per (n, residual) and replayed; the descriptor table it reads is rewritten
+ * in device memory before each replay, so lattices can be attached and detached
+ * between calls without recapturing.
+ * --------------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch; /* opaque; owned by the library */
+
+typedef struct {
+  int capacity;             /* slots */
+  int attached;             /* slots in use */
+  int grid;                 /* thread blocks of the persistent launch */
+  int64_t nodes;            /* nodes of all attached lattices */
+  int64_t steps;            /* batched steps taken */
+  int64_t kernel_launches;  /* kernels the batch has launched (sweeps + reductions) */
+  int64_t device_bytes;     /* device memory the batch itself holds (its table) */
+} lbm_batch_info_t;
+
+/* A batch of `capacity` slots for contexts of precision `prec` on the current device.
+ * Work runs on a stream the batch creates (see lbm_batch_set_stream). */
+LBM_API lbm_status lbm_batch_create(int capacity, lbm_precision prec, lbm_batch** out);
+
+/* Synchronise, detach every context (the contexts stay valid) and free the batch. */
+LBM_API lbm_status lbm_batch_destroy(lbm_batch* b);
+
+/* Issue later batch work on `cuda_stream` (NULL = legacy default stream, on which the
+ * steps are launched directly instead of through a CUDA graph). Synchronises the
+ * previous stream. */
+LBM_API lbm_status lbm_batch_set_stream(lbm_batch* b, void* cuda_stream);
+
+/* Put `ctx` into `slot` (0 <= slot < capacity, empty). The context must have the
+ * batch's precision and device and belong to no other batch. Waits for the context's
+ * own stream and allocates its residual buffers. While attached, the context's own
+ * calls (lbm_step, lbm_macros, ...) first wait for the batch's stream; lbm_destroy
+ * detaches it. */
+LBM_API lbm_status lbm_batch_attach(lbm_batch* b, int slot, lbm_ctx* ctx);
+
+/* Empty `slot` after the batch's queued work has finished (synchronises). */
+LBM_API lbm_status lbm_batch_detach(lbm_batch* b, int slot);
+
+/* Advance every attached lattice by n >= 1 time steps (as lbm_step), asynchronously on
+ * the batch's stream. With residual != 0 the last step also forms each lattice's
+ * residual and mass exactly as lbm_step_residual does (same snapshot semantics); read
+ * them with lbm_batch_results. */
+LBM_API lbm_status lbm_batch_step(lbm_batch* b, int n, int residual);
+
+/* Per slot (arrays of `capacity`, any may be NULL): residual and mass of the last
+ * lbm_batch_step with residual != 0, and a status: LBM_OK, LBM_ERR_DIVERGED (as in
+ * lbm_step_residual), or 1 when the slot has no result (empty, or attached after that
+ * step). Synchronises. */
+LBM_API lbm_status lbm_batch_results(lbm_batch* b, double* residual, double* mass, int* status);
+
+LBM_API lbm_status lbm_batch_info(const lbm_batch* b, lbm_batch_info_t* out);
+
+/* Last error message of a batch (or of the calling thread when b is NULL). */
+LBM_API const char* lbm_batch_last_error(const lbm_batch* b);
+
 /* Reduction of a caller-held population array that allocates nothing (the paper has no
  * counterpart; it is the state reduction of lbm_residual without a context).
  *

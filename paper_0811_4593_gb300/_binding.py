@@ -38,6 +38,15 @@ EXPORTS = {
     "lbm_sync": (C.c_int, [C.c_void_p]),
     "lbm_info": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
+    "lbm_batch_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "lbm_batch_destroy": (C.c_int, [C.c_void_p]),
+    "lbm_batch_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lbm_batch_attach": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "lbm_batch_detach": (C.c_int, [C.c_void_p, C.c_int]),
+    "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "lbm_batch_results": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_batch_info": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lbm_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_reduce_state_static": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p,
                                           C.c_void_p, C.c_void_p]),
 }
@@ -300,3 +309,82 @@ class Lattice:
         i = Info()
         check(lib().lbm_info(self.ctx, C.byref(i)), self.ctx)
         return {f: getattr(i, f) for f, _ in Info._fields_}
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("capacity", C.c_int), ("attached", C.c_int), ("grid", C.c_int), ("nodes", C.c_int64),
+                ("steps", C.c_int64), ("kernel_launches", C.c_int64), ("device_bytes", C.c_int64)]
+
+
+class Batch:
+    """Slots of resident lattices advanced together by one persistent launch per step
+    (CUDA-graph replays of the n-step loop). Attach Lattice objects of the batch's
+    precision; results of residual steps come back per slot."""
+
+    NO_RESULT = 1
+
+    def __init__(self, capacity: int, precision: str = "f32", stream=None, torch_allocator=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: batches run only on the GPU")
+        if torch_allocator:
+            use_torch_allocator()
+        self.capacity = int(capacity)
+        self.precision = precision
+        out = C.c_void_p()
+        st = lib().lbm_batch_create(self.capacity, PRECISIONS[precision], C.byref(out))
+        if st != LBM_OK:
+            raise LBMError(st, lib().lbm_batch_last_error(None).decode())
+        self._b = out
+        self.lattices = [None] * self.capacity
+        if stream is not None:
+            self._check(lib().lbm_batch_set_stream(self._b, C.c_void_p(stream.cuda_stream)))
+        self._r = (C.c_double * self.capacity)()
+        self._m = (C.c_double * self.capacity)()
+        self._s = (C.c_int * self.capacity)()
+
+    def _check(self, st):
+        if st != LBM_OK:
+            raise LBMError(st, lib().lbm_batch_last_error(self._b).decode())
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().lbm_batch_destroy(self._b)
+            self._b = None
+            self.lattices = [None] * self.capacity
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def attach(self, slot: int, lattice: "Lattice"):
+        self._check(lib().lbm_batch_attach(self._b, int(slot), lattice.ctx))
+        self.lattices[slot] = lattice
+
+    def detach(self, slot: int):
+        self._check(lib().lbm_batch_detach(self._b, int(slot)))
+        self.lattices[slot] = None
+
+    def free_slots(self):
+        return [i for i, l in enumerate(self.lattices) if l is None]
+
+    def step(self, n: int, residual: bool = False):
+        self._check(lib().lbm_batch_step(self._b, int(n), 1 if residual else 0))
+
+    def results(self):
+        """[(residual, mass, status)] per slot; status 0 ok, -4 diverged, 1 no result."""
+        self._check(lib().lbm_batch_results(self._b, self._r, self._m, self._s))
+        return [(self._r[i], self._m[i], self._s[i]) for i in range(self.capacity)]
+
+    def info(self) -> dict:
+        i = BatchInfo()
+        self._check(lib().lbm_batch_info(self._b, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in BatchInfo._fields_}

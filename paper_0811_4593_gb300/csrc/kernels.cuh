@@ -1,13 +1,13 @@
 // kernels.cuh -- fused D3Q19 sweep and its companion kernels, templated on the
 // storage type S (double, float, __half). Included by one translation unit per S.
 //
-// In registers every population is carried shifted, h_i = f_i - w_i rho0. The
-// closure and collision rules are linear in f with weights that sum to one where a
-// density is formed, so they hold unchanged for h (sum_i w_i c_i = 0 and the density
-// relation's weights sum to 1); the shift keeps the small deviations from rest at
-// full precision in float arithmetic. FP64 storage holds f_i; FP32 and binary16
-// storage hold h_i, so their rounding is relative to the small deviation from rest
-// rather than to f_i itself.
+// FP32 and binary16 storage hold the shifted populations h_i = f_i - w_i rho0 and the
+// sweep carries them shifted in registers, so float rounding is relative to the small
+// deviation from rest rather than to f_i. The closure and collision rules hold
+// unchanged for h (sum_i w_i c_i = 0, and the weights of the density relation sum to
+// one), with every density written as rho0 + (sum of h). FP64 storage holds f_i itself;
+// the same code runs on it with the reference density 0 (then "sum of h" is rho), which
+// spares the FP64 pipe the 38 shift additions per node.
 #pragma once
 #include <cuda_fp16.h>
 #include <type_traits>
@@ -29,52 +29,81 @@ __device__ __forceinline__ void static_for(F&& f) {
 template <typename S> struct ComputeOf { using T = float; };
 template <> struct ComputeOf<double> { using T = double; };
 
-// Storage codec: stored value <-> shifted population h in the compute type.
-template <typename S> struct Codec;
-template <> struct Codec<double> {
-  __device__ static double load(const double* p, double shift) { return __ldg(p) - shift; }
-  __device__ static double store(double h, double shift) { return h + shift; }
+// Storage codec: stored value <-> register value v (h_i for shifted storage, f_i for
+// FP64) in the compute type.
+template <typename S> struct Storage;
+template <> struct Storage<double> {
+  static constexpr bool shifted = false;
+  __device__ static double load(const double* p) { return __ldg(p); }
+  __device__ static double store(double v) { return v; }
 };
-template <> struct Codec<float> {
-  __device__ static float load(const float* p, float) { return __ldg(p); }
-  __device__ static float store(float h, float) { return h; }
+template <> struct Storage<float> {
+  static constexpr bool shifted = true;
+  __device__ static float load(const float* p) { return __ldg(p); }
+  __device__ static float store(float v) { return v; }
 };
-template <> struct Codec<__half> {
-  __device__ static float load(const __half* p, float) { return __half2float(__ldg(p)); }
-  __device__ static __half store(float h, float) { return __float2half_rn(h); }
+template <> struct Storage<__half> {
+  static constexpr bool shifted = true;
+  __device__ static float load(const __half* p) { return __half2float(__ldg(p)); }
+  __device__ static __half store(float v) { return __float2half_rn(v); }
 };
 
-// shift_k = w_k rho0 in the compute type, for the three weight classes
-template <typename T>
-struct Shifts {
-  T axis, diag, rest;
-  __device__ explicit Shifts(double rho0)
-      : axis(T(wgt<double>(0) * rho0)), diag(T(wgt<double>(6) * rho0)), rest(T(wgt<double>(18) * rho0)) {}
-  template <int k> __device__ T get() const { return k < 6 ? axis : (k < 18 ? diag : rest); }
-};
+// The reference density the register values are shifted by: rho0, or 0 for FP64.
+template <typename S>
+__device__ __forceinline__ double ref_rho(double rho0) { return Storage<S>::shifted ? rho0 : 0.0; }
 
 // ---------------------------------------------------------------------------------
 // Boundary closures on the shifted populations h (readings identical to the FP64
 // oracle; see the header of each rule).
 // ---------------------------------------------------------------------------------
 
+// Error-free accumulation of a float sum as hi + lo (Knuth's TwoSum); the rounded
+// intrinsics keep the compiler from contracting or reassociating the steps.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float t) {
+  const float s = __fadd_rn(hi, t);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(t, bb));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
+// Velocity of a face node in the compute type, and 1 / (1 - u.n) in double.
+template <typename T>
+struct FaceVals {
+  T u[3];
+  double inv;
+};
+
 // On-site velocity closure of a plane with inward normal SG * e_A: density from the
 // in-plane populations and twice the outgoing ones (eq. uin and the appendix
-// relations, formed in double), transverse corrections N on the two tangential axes
-// (eqs. Nx, Ny and analogues), and for every unknown population i (c_i.n > 0)
+// relations), transverse corrections N on the two tangential axes (eqs. Nx, Ny and
+// analogues), and for every unknown population i (c_i.n > 0)
 //   h_i = h_-i + 6 w_i rho c_i.u - t_i.N     (eq. f5, eqs. f9-f17, appendix).
+// The density is formed in double: rho = (rho0 + S) / (1 - u.n), where S, the
+// relation's sum over the shifted populations (its weights sum to 1), is exact in
+// double (accumulated in double for FP64, as an error-free float pair otherwise).
 template <int A, int SG, typename T>
-__device__ __forceinline__ void close_face(T (&h)[Q], const double (&u)[3], double rho0) {
-  double s = 0.0;
-  static_for<0, Q>([&](auto kc) {
-    constexpr int k = decltype(kc)::value;
-    constexpr int cn = SG * ca(k, A);
-    if constexpr (cn == 0) s += double(h[k]);
-    else if constexpr (cn < 0) s += 2.0 * double(h[k]);
-  });
-  // sum over the relation's weights is 1, so sum f = rho0 + sum h
-  const double rho_d = (rho0 + s) / (1.0 - double(SG) * u[A]);
-  const T rho = T(rho_d);
+__device__ __forceinline__ void close_face(T (&h)[Q], const FaceVals<T>& fv, double rho0) {
+  double S;
+  if constexpr (std::is_same<T, double>::value) {
+    S = 0.0;
+    static_for<0, Q>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      constexpr int cn = SG * ca(k, A);
+      if constexpr (cn == 0) S += h[k];
+      else if constexpr (cn < 0) S += 2.0 * h[k];
+    });
+  } else {
+    float hi = 0.0f, lo = 0.0f;
+    static_for<0, Q>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      constexpr int cn = SG * ca(k, A);
+      if constexpr (cn == 0) two_sum_acc(hi, lo, h[k]);
+      else if constexpr (cn < 0) two_sum_acc(hi, lo, __fmul_rn(2.0f, h[k]));
+    });
+    S = double(hi) + double(lo);
+  }
+  const T rho = T((rho0 + S) * fv.inv);
   constexpr int B = (A == 0) ? 1 : 0;
   constexpr int C = (A == 2) ? 1 : 2;
   T sb = T(0), sc = T(0);
@@ -86,14 +115,13 @@ __device__ __forceinline__ void close_face(T (&h)[Q], const double (&u)[3], doub
     }
   });
   const T third = T(1) / T(3);
-  const T NB = T(0.5) * sb - rho * T(u[B]) * third;
-  const T NC = T(0.5) * sc - rho * T(u[C]) * third;
-  const T ux = T(u[0]), uy = T(u[1]), uz = T(u[2]);
+  const T NB = T(0.5) * sb - rho * fv.u[B] * third;
+  const T NC = T(0.5) * sc - rho * fv.u[C] * third;
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     if constexpr (SG * ca(k, A) > 0) {
       constexpr int m = opp(k);
-      const T cu = T(cx(k)) * ux + T(cy(k)) * uy + T(cz(k)) * uz;
+      const T cu = T(cx(k)) * fv.u[0] + T(cy(k)) * fv.u[1] + T(cz(k)) * fv.u[2];
       const T coef = T(6 * w36(k)) / T(36);
       T t = T(0);
       if constexpr (ca(k, B) != 0) t += T(ca(k, B)) * NB;
@@ -186,32 +214,52 @@ __device__ __forceinline__ void close_corner(T (&h)[Q]) {
   h[Q - 1] = T(12) * fb;
 }
 
-// Prescribed velocity of face (A, SG) at node (x, y, z).
-template <int A, int SG>
-__device__ __forceinline__ void face_velocity(const SweepArgs& a, uint32_t x, uint32_t y, uint32_t z,
-                                              double (&u)[3]) {
+// Prescribed velocity of face (A, SG) at node (x, y, z): from the face's node table
+// when it has one, else the face's uniform value.
+template <int A, int SG, typename T>
+__device__ __forceinline__ FaceVals<T> face_values(const SweepArgs& a, uint32_t x, uint32_t y, uint32_t z) {
   constexpr int f = 2 * A + (SG > 0 ? 0 : 1);
-  const double* tab = a.face[f].tab;
-  if (tab) {
+  const FaceBC& fb = a.face[f];
+  FaceVals<T> v;
+  if (fb.tab) {
     const uint32_t t1 = (A == 0) ? y : x;
     const uint32_t t2 = (A == 2) ? y : z;
     const uint32_t n1 = (A == 0) ? a.ny : a.nx;
-    const double* p = tab + 3ull * (size_t(t2) * n1 + t1);
-    u[0] = __ldg(p);
-    u[1] = __ldg(p + 1);
-    u[2] = __ldg(p + 2);
+    const FaceNode* p = fb.tab + (size_t(t2) * n1 + t1);
+    if constexpr (std::is_same<T, double>::value) {
+      const double2 a0 = __ldg(reinterpret_cast<const double2*>(p));
+      const double2 a1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+      v.u[0] = a0.x;
+      v.u[1] = a0.y;
+      v.u[2] = a1.x;
+      v.inv = a1.y;
+    } else {
+      const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 2);
+      v.u[0] = b.x;
+      v.u[1] = b.y;
+      v.u[2] = b.z;
+      v.inv = __ldg(&p->inv);
+    }
   } else {
-    u[0] = a.face[f].u[0];
-    u[1] = a.face[f].u[1];
-    u[2] = a.face[f].u[2];
+    if constexpr (std::is_same<T, double>::value) {
+      v.u[0] = fb.uni.u[0];
+      v.u[1] = fb.uni.u[1];
+      v.u[2] = fb.uni.u[2];
+    } else {
+      v.u[0] = fb.uni.uf[0];
+      v.u[1] = fb.uni.uf[1];
+      v.u[2] = fb.uni.uf[2];
+    }
+    v.inv = fb.uni.inv;
   }
+  return v;
 }
 
 template <int A, int SG, typename T>
 __device__ __forceinline__ void face_case(const SweepArgs& a, uint32_t x, uint32_t y, uint32_t z, T (&h)[Q]) {
-  double u[3];
-  face_velocity<A, SG>(a, x, y, z, u);
-  close_face<A, SG>(h, u, a.rho0);
+  // reference density of the register values: 0 for FP64 (unshifted), rho0 otherwise
+  const double ref = std::is_same<T, double>::value ? 0.0 : a.rho0;
+  close_face<A, SG>(h, face_values<A, SG, T>(a, x, y, z), ref);
 }
 
 // code = fx + 3 fy + 9 fz with f = 0 (interior or periodic), 1 (low face), 2 (high face)
@@ -259,11 +307,11 @@ __device__ __forceinline__ void apply_boundary(int code, const SweepArgs& a, uin
 //   h_i^eq = w_i (drho + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u^2)).
 template <typename T>
 struct Moments {
-  T drho, rho, ux, uy, uz;
+  T drho, rho, jx, jy, jz, ux, uy, uz;  // drho = sum of v; rho = ref + drho; j = rho u
 };
 
 template <typename T>
-__device__ __forceinline__ Moments<T> moments(const T (&h)[Q], double rho0) {
+__device__ __forceinline__ Moments<T> moments(const T (&h)[Q], T rho0) {
   T d = T(0), jx = T(0), jy = T(0), jz = T(0);
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
@@ -274,7 +322,10 @@ __device__ __forceinline__ Moments<T> moments(const T (&h)[Q], double rho0) {
   });
   Moments<T> m;
   m.drho = d;
-  m.rho = T(rho0) + d;
+  m.rho = rho0 + d;
+  m.jx = jx;
+  m.jy = jy;
+  m.jz = jz;
   const T inv = T(1) / m.rho;
   m.ux = jx * inv;
   m.uy = jy * inv;
@@ -282,19 +333,43 @@ __device__ __forceinline__ Moments<T> moments(const T (&h)[Q], double rho0) {
   return m;
 }
 
+// BGK relaxation v_i <- (1 - omega) v_i + omega v_i^eq with the second-order
+// equilibrium written for the pair (i, -i), whose c.u only changes sign:
+//   v^eq_{+-i} = w_i (b + s_i +- a_i),  b = drho - 3/2 j.u,  s_i = 9/2 (c_i.j)(c_i.u),
+//   a_i = 3 c_i.j
+// (j = rho u), which equals w_i (drho + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u^2)) (eq. feq)
+// term by term and shares the symmetric part between the two populations.
 template <typename T>
 __device__ __forceinline__ void collide(T (&h)[Q], const Moments<T>& m, T omega) {
-  const T usq15 = T(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+  const T b = m.drho - T(1.5) * (m.jx * m.ux + m.jy * m.uy + m.jz * m.uz);
+  const T keep = T(1) - omega;
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    T cu = T(0);
-    if constexpr (cx(k) != 0) cu += T(cx(k)) * m.ux;
-    if constexpr (cy(k) != 0) cu += T(cy(k)) * m.uy;
-    if constexpr (cz(k) != 0) cu += T(cz(k)) * m.uz;
-    const T heq = wgt<T>(k) * (m.drho + m.rho * (T(3) * cu + T(4.5) * cu * cu - usq15));
-    h[k] = h[k] - omega * (h[k] - heq);
+    constexpr int o = opp(k);
+    if constexpr (k == Q - 1) {
+      h[k] = keep * h[k] + (omega * wgt<T>(k)) * b;
+    } else if constexpr (k < o) {
+      T cj = T(0), cu = T(0);
+      if constexpr (cx(k) != 0) { cj += T(cx(k)) * m.jx; cu += T(cx(k)) * m.ux; }
+      if constexpr (cy(k) != 0) { cj += T(cy(k)) * m.jy; cu += T(cy(k)) * m.uy; }
+      if constexpr (cz(k) != 0) { cj += T(cz(k)) * m.jz; cu += T(cz(k)) * m.uz; }
+      const T t = b + T(4.5) * cj * cu;
+      const T a = T(3) * cj;
+      const T ow = omega * wgt<T>(k);
+      h[k] = keep * h[k] + ow * (t + a);
+      h[o] = keep * h[o] + ow * (t - a);
+    }
   });
 }
+
+// Launch parameters in the compute type (no per-node double-to-float conversion);
+// rho0_of is the reference density of the register values (0 for FP64 storage).
+template <typename T> __device__ __forceinline__ T rho0_of(const SweepArgs& a);
+template <> __device__ __forceinline__ double rho0_of<double>(const SweepArgs&) { return 0.0; }
+template <> __device__ __forceinline__ float rho0_of<float>(const SweepArgs& a) { return a.rho0f; }
+template <typename T> __device__ __forceinline__ T omega_of(const SweepArgs& a);
+template <> __device__ __forceinline__ double omega_of<double>(const SweepArgs& a) { return a.omega; }
+template <> __device__ __forceinline__ float omega_of<float>(const SweepArgs& a) { return a.omegaf; }
 
 // Deterministic block sum of four doubles; thread 0 of the block gets the totals.
 __device__ __forceinline__ void block_sum4(double (&v)[4], double* out) {
@@ -341,10 +416,11 @@ __device__ __forceinline__ void residual_terms(const Moments<T>& m, double rho0,
 // ---------------------------------------------------------------------------------
 // The fused time step: pull stream, classify, close, collide, store.
 // ---------------------------------------------------------------------------------
+// Block `blk` (nodes blk*256 .. blk*256+255) of the lattice described by `a`.
 template <typename S, bool RESID>
-__global__ void __launch_bounds__(SWEEP_THREADS) sweep_kernel(const SweepArgs a) {
+__device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
   using T = typename ComputeOf<S>::T;
-  const uint32_t cell = blockIdx.x * SWEEP_THREADS + threadIdx.x;
+  const uint32_t cell = blk * SWEEP_THREADS + threadIdx.x;
   const bool active = cell < a.N;
   double red[4] = {0.0, 0.0, 0.0, 0.0};
   if (active) {
@@ -364,7 +440,6 @@ __global__ void __launch_bounds__(SWEEP_THREADS) sweep_kernel(const SweepArgs a)
     const uint32_t zp = (z + 1 < a.nz) ? z + 1 : (pz ? 0 : a.nz - 1);
     const S* __restrict__ src = static_cast<const S*>(a.src);
     S* __restrict__ dst = static_cast<S*>(a.dst);
-    const Shifts<T> sh(a.rho0);
     T h[Q];
     static_for<0, Q>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
@@ -372,22 +447,90 @@ __global__ void __launch_bounds__(SWEEP_THREADS) sweep_kernel(const SweepArgs a)
       const uint32_t sy = cy(k) > 0 ? ym : (cy(k) < 0 ? yp : y);
       const uint32_t sz = cz(k) > 0 ? zm : (cz(k) < 0 ? zp : z);
       const uint32_t idx = (sz * a.ny + sy) * a.nx + sx;
-      h[k] = Codec<S>::load(src + size_t(k) * a.N + idx, sh.template get<k>());
+      h[k] = Storage<S>::load(src + size_t(k) * a.N + idx);
     });
     const int fx = px ? 0 : (x == 0 ? 1 : (x == a.nx - 1 ? 2 : 0));
     const int fy = py ? 0 : (y == 0 ? 1 : (y == a.ny - 1 ? 2 : 0));
     const int fz = pz ? 0 : (z == 0 ? 1 : (z == a.nz - 1 ? 2 : 0));
     const int code = fx + 3 * fy + 9 * fz;
     if (code != 0) apply_boundary(code, a, x, y, z, h);
-    const Moments<T> m = moments(h, a.rho0);
-    if constexpr (RESID) residual_terms(m, a.rho0, static_cast<T*>(a.snap), a.N, cell, red);
-    collide(h, m, T(a.omega));
+    const Moments<T> m = moments(h, rho0_of<T>(a));
+    if constexpr (RESID) residual_terms(m, ref_rho<S>(a.rho0), static_cast<T*>(a.snap), a.N, cell, red);
+    collide(h, m, omega_of<T>(a));
     static_for<0, Q>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
-      dst[size_t(k) * a.N + cell] = Codec<S>::store(h[k], sh.template get<k>());
+      dst[size_t(k) * a.N + cell] = Storage<S>::store(h[k]);
     });
   }
-  if constexpr (RESID) block_sum4(red, a.partials + 4ull * blockIdx.x);
+  if constexpr (RESID) block_sum4(red, a.partials + 4ull * blk);
+}
+
+// Resident 256-thread blocks per SM each sweep variant is compiled for (the register
+// budget is 65536 / (256 * blocks)). The float sweeps are memory-bound and need many
+// warps in flight to hide DRAM latency: 6 blocks (<= 42 registers) for the plain
+// single-lattice step; the residual and batched variants carry more state and get one
+// or two blocks fewer so that they do not spill. The FP64 sweeps are bound by the
+// FP64 pipe and get room for their double registers.
+template <typename S, bool RESID, bool BATCHED>
+struct SweepOccupancy {
+  static constexpr int blocks = 6 - (RESID ? 1 : 0) - (BATCHED ? 1 : 0);
+};
+template <bool RESID, bool BATCHED>
+struct SweepOccupancy<double, RESID, BATCHED> {
+  static constexpr int blocks = (RESID && BATCHED) ? 2 : 3;
+};
+
+template <typename S, bool RESID>
+__global__ void __launch_bounds__(SWEEP_THREADS, (SweepOccupancy<S, RESID, false>::blocks))
+    sweep_kernel(const __grid_constant__ SweepArgs a) {
+  sweep_block<S, RESID>(a, blockIdx.x);
+}
+
+// One time step of every lattice of a batch. A persistent grid splits the batch's
+// global block range into one contiguous share per CTA; a CTA caches the descriptor of
+// the lattice it is in (in shared memory) and runs the same per-block code as the
+// single-lattice sweep, so every lattice computes the same bits alone or in a batch.
+template <typename S, bool RESID>
+__global__ void __launch_bounds__(SWEEP_THREADS, (SweepOccupancy<S, RESID, true>::blocks))
+    sweep_batched_kernel(const BatchHeader* __restrict__ hdr, const BatchEntry* __restrict__ ents, uint32_t parity) {
+  __shared__ SweepArgs sa;
+  __shared__ uint32_t s_idx;
+  const uint32_t total = hdr->total_blocks;
+  const uint32_t nent = hdr->nentries;
+  uint32_t b = uint32_t(uint64_t(blockIdx.x) * total / gridDim.x);
+  const uint32_t bend = uint32_t(uint64_t(blockIdx.x + 1) * total / gridDim.x);
+  uint32_t lat_begin = 0, lat_end = 0;
+  while (b < bend) {
+    if (b >= lat_end) {
+      __syncthreads();  // every thread is done with the previous descriptor
+      if (threadIdx.x == 0) {
+        uint32_t lo = 0, hi = nent;  // last entry with block_begin <= b
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (ents[mid].block_begin <= b) lo = mid;
+          else hi = mid;
+        }
+        s_idx = lo;
+      }
+      __syncthreads();
+      const BatchEntry* e = ents + s_idx;
+      const uint32_t* from = reinterpret_cast<const uint32_t*>(&e->a);
+      uint32_t* to = reinterpret_cast<uint32_t*>(&sa);
+      for (uint32_t w = threadIdx.x; w < sizeof(SweepArgs) / 4; w += SWEEP_THREADS) to[w] = from[w];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const uint32_t c = (e->cur ^ parity) & 1u;
+        sa.src = e->buf[c];
+        sa.dst = const_cast<void*>(e->buf[c ^ 1u]);
+      }
+      lat_begin = e->block_begin;
+      lat_end = e->block_begin + e->nblocks;
+      __syncthreads();
+    }
+    sweep_block<S, RESID>(sa, b - lat_begin);
+    if constexpr (RESID) __syncthreads();  // the block-sum buffer is reused by the next block
+    ++b;
+  }
 }
 
 // Stored state -> residual terms (no streaming, no update).
@@ -398,14 +541,14 @@ __global__ void __launch_bounds__(SWEEP_THREADS)
   const uint32_t cell = blockIdx.x * SWEEP_THREADS + threadIdx.x;
   double red[4] = {0.0, 0.0, 0.0, 0.0};
   if (cell < N) {
-    const Shifts<T> sh(rho0);
     T h[Q];
     static_for<0, Q>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
-      h[k] = Codec<S>::load(src + size_t(k) * N + cell, sh.template get<k>());
+      h[k] = Storage<S>::load(src + size_t(k) * N + cell);
     });
-    const Moments<T> m = moments(h, rho0);
-    residual_terms(m, rho0, static_cast<T*>(snap), N, cell, red);
+    const double ref = ref_rho<S>(rho0);
+    const Moments<T> m = moments(h, T(ref));
+    residual_terms(m, ref, static_cast<T*>(snap), N, cell, red);
   }
   block_sum4(red, partials + 4ull * blockIdx.x);
 }
@@ -415,10 +558,11 @@ __global__ void __launch_bounds__(SWEEP_THREADS) init_kernel(S* __restrict__ dst
   using T = typename ComputeOf<S>::T;
   const uint32_t cell = blockIdx.x * SWEEP_THREADS + threadIdx.x;
   if (cell >= N) return;
-  const Shifts<T> sh(rho0);
+  // f = f_eq(rho0, 0) = w_i rho0; shifted storage holds 0
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    dst[size_t(k) * N + cell] = Codec<S>::store(T(0), sh.template get<k>());
+    const T v = Storage<S>::shifted ? T(0) : T(wgt<double>(k) * rho0);
+    dst[size_t(k) * N + cell] = Storage<S>::store(v);
   });
 }
 
@@ -429,13 +573,12 @@ __global__ void __launch_bounds__(SWEEP_THREADS)
   using T = typename ComputeOf<S>::T;
   const uint32_t cell = blockIdx.x * SWEEP_THREADS + threadIdx.x;
   if (cell >= N) return;
-  const Shifts<T> sh(rho0);
   T h[Q];
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    h[k] = Codec<S>::load(src + size_t(k) * N + cell, sh.template get<k>());
+    h[k] = Storage<S>::load(src + size_t(k) * N + cell);
   });
-  const Moments<T> m = moments(h, rho0);
+  const Moments<T> m = moments(h, T(ref_rho<S>(rho0)));
   if (rho) rho[cell] = m.rho;
   if (u) {
     u[cell] = m.ux;
@@ -477,6 +620,26 @@ cudaError_t launch_state_reduce_impl(const void* src, uint32_t N, double rho0, v
   return cudaGetLastError();
 }
 
+template <typename S>
+cudaError_t launch_sweep_batched_impl(const BatchHeader* hdr, const BatchEntry* ents, uint32_t parity, bool resid,
+                                      int grid, cudaStream_t s) {
+  if (resid) sweep_batched_kernel<S, true><<<grid, SWEEP_THREADS, 0, s>>>(hdr, ents, parity);
+  else sweep_batched_kernel<S, false><<<grid, SWEEP_THREADS, 0, s>>>(hdr, ents, parity);
+  return cudaGetLastError();
+}
+
+template <typename S>
+int batched_grid_impl() {
+  int dev = 0, sms = 0, a = 0, b = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sweep_batched_kernel<S, false>, SWEEP_THREADS, 0) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_batched_kernel<S, true>, SWEEP_THREADS, 0) != cudaSuccess)
+    return 0;
+  return sms * (a < b ? a : b);
+}
+
 #define LBM_INSTANTIATE(S)                                                                              \
   template <> cudaError_t launch_sweep<S>(const SweepArgs& a, bool resid, cudaStream_t s) {             \
     return launch_sweep_impl<S>(a, resid, s);                                                           \
@@ -491,6 +654,11 @@ cudaError_t launch_state_reduce_impl(const void* src, uint32_t N, double rho0, v
   template <> cudaError_t launch_state_reduce<S>(const void* src, uint32_t N, double rho0, void* snap,  \
                                                  double* partials, cudaStream_t s) {                   \
     return launch_state_reduce_impl<S>(src, N, rho0, snap, partials, s);                                \
-  }
+  }                                                                                                     \
+  template <> cudaError_t launch_sweep_batched<S>(const BatchHeader* hdr, const BatchEntry* ents,       \
+                                                  uint32_t parity, bool resid, int grid, cudaStream_t s) { \
+    return launch_sweep_batched_impl<S>(hdr, ents, parity, resid, grid, s);                            \
+  }                                                                                                     \
+  template <> int batched_grid<S>() { return batched_grid_impl<S>(); }
 
 }  // namespace lbm

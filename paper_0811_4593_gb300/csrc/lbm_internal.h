@@ -32,10 +32,20 @@ __device__ __forceinline__ uint32_t fdiv(const FastDiv& f, uint32_t n) {
 }
 #endif
 
+// Prescribed velocity of one velocity-face node as the sweep reads it: the velocity in
+// double and float, and 1 / (1 - u.n) for the density relation (n = inward normal),
+// formed in double on the host.
+struct __align__(16) FaceNode {
+  double u[3];
+  double inv;
+  float uf[3];
+  float pad;
+};
+
 // Boundary data of one face for the sweep.
 struct FaceBC {
-  const double* tab;  // device [n2][n1][3] or nullptr (uniform u)
-  double u[3];
+  const FaceNode* tab;  // device [n2][n1] or nullptr (uniform: `uni`)
+  FaceNode uni;
 };
 
 // Everything one sweep launch needs, passed by value.
@@ -47,9 +57,26 @@ struct SweepArgs {
   uint32_t periodic;  // bit a set: axis a is periodic
   double rho0;
   double omega;       // 1 / tau
+  float rho0f, omegaf;
   FaceBC face[6];
   void* snap;         // residual steps: [3][N] velocity snapshot in the compute type
   double* partials;   // residual steps: [blocks][4] per-block sums
+};
+
+// One lattice of a batch, as the batched sweep reads it from device memory.
+struct BatchEntry {
+  SweepArgs a;           // src/dst are taken from buf[] and the step parity
+  const void* buf[2];    // the lattice's two population buffers
+  uint32_t cur;          // index into buf[] of the current state at step parity 0
+  uint32_t block_begin;  // first global block of this lattice in the batch
+  uint32_t nblocks;      // 256-node blocks of this lattice
+  uint32_t slot;         // row of the batch's result table
+};
+
+struct BatchHeader {
+  uint32_t nentries;      // entries in use, ordered by block_begin
+  uint32_t total_blocks;  // sum of nblocks
+  uint32_t pad[2];
 };
 
 constexpr int SWEEP_THREADS = 256;
@@ -64,6 +91,11 @@ template <typename S> cudaError_t launch_macros(const void* src, uint32_t N, dou
 template <typename S> cudaError_t launch_state_reduce(const void* src, uint32_t N, double rho0,
                                                       void* snap, double* partials, cudaStream_t s);
 cudaError_t launch_final_reduce(const double* partials, uint32_t nblocks, double* out, cudaStream_t s);
+template <typename S> cudaError_t launch_sweep_batched(const BatchHeader* hdr, const BatchEntry* ents, uint32_t parity,
+                                                       bool resid, int grid, cudaStream_t s);
+template <typename S> int batched_grid();  // persistent grid size: SMs x resident blocks per SM
+cudaError_t launch_batch_final_reduce(const BatchHeader* hdr, const BatchEntry* ents, int capacity, double* results,
+                                      cudaStream_t s);
 
 // Sets the calling thread's context-free error message (lbm_last_error(NULL)).
 void record_error(const char* msg);

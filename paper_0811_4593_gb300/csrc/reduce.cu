@@ -1,32 +1,31 @@
-// reduce.cu -- fixed-order final reduction of per-block partial sums.
-#include "lbm_internal.h"
+// reduce.cu -- final reduction of one lattice's per-block partial sums.
+#include "reduce.cuh"
 
 namespace lbm {
 
-// One block folds partials[nblocks][4] into out[4]: thread t sums blocks t, t+1024, ...
-// in ascending order, then a fixed pairwise tree over the threads. The order depends
-// only on nblocks, so a lattice reduces to the same bits wherever it is computed.
 __global__ void __launch_bounds__(REDUCE_THREADS)
     final_reduce_kernel(const double* __restrict__ partials, uint32_t nblocks, double* __restrict__ out) {
-  __shared__ double s[4][REDUCE_THREADS];
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  for (uint32_t b = threadIdx.x; b < nblocks; b += REDUCE_THREADS)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] += partials[4ull * b + j];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) s[j][threadIdx.x] = v[j];
-  __syncthreads();
-  for (int w = REDUCE_THREADS / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) s[j][threadIdx.x] += s[j][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x < 4) out[threadIdx.x] = s[threadIdx.x][0];
+  fold_partials(partials, nblocks, out);
 }
 
 cudaError_t launch_final_reduce(const double* partials, uint32_t nblocks, double* out, cudaStream_t s) {
   final_reduce_kernel<<<1, REDUCE_THREADS, 0, s>>>(partials, nblocks, out);
+  return cudaGetLastError();
+}
+
+// Final reduction of every lattice of a batch: block i folds entry i's partials into
+// results[slot][4]; blocks past the entries in use return at once.
+__global__ void __launch_bounds__(REDUCE_THREADS)
+    batch_final_reduce_kernel(const BatchHeader* __restrict__ hdr, const BatchEntry* __restrict__ ents,
+                              double* __restrict__ results) {
+  if (blockIdx.x >= hdr->nentries) return;
+  const BatchEntry& e = ents[blockIdx.x];
+  fold_partials(e.a.partials, e.nblocks, results + 4ull * e.slot);
+}
+
+cudaError_t launch_batch_final_reduce(const BatchHeader* hdr, const BatchEntry* ents, int capacity, double* results,
+                                      cudaStream_t s) {
+  batch_final_reduce_kernel<<<capacity, REDUCE_THREADS, 0, s>>>(hdr, ents, results);
   return cudaGetLastError();
 }
 

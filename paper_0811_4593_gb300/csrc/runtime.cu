@@ -47,6 +47,40 @@ struct lbm_ctx {
   lbm_free_fn release = nullptr;
   void* user = nullptr;
   std::vector<Allocation> allocations;
+  lbm_batch* batch = nullptr;  // batch the context is attached to, if any
+  int batch_slot = -1;
+};
+
+struct lbm_batch {
+  int device = 0;
+  int capacity = 0;
+  lbm_precision prec = LBM_F32;
+  std::vector<lbm_ctx*> slots;
+  std::vector<uint8_t> has_result;  // slot took part in the last residual step
+  lbm::BatchHeader* h_hdr = nullptr;  // pinned host mirror of the device table
+  lbm::BatchEntry* h_ent = nullptr;
+  double* h_res = nullptr;            // pinned [capacity][4]
+  lbm::BatchHeader* d_hdr = nullptr;
+  lbm::BatchEntry* d_ent = nullptr;
+  double* d_res = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t table_free = nullptr;  // the last table upload has read the host mirror
+  int grid = 0;
+  uint32_t total_blocks = 0;
+  struct Graph {
+    int n;
+    bool resid;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  bool results_valid = false;
+  int64_t steps = 0, launches = 0, device_bytes = 0;
+  std::string err = "no error";
+  lbm_alloc_fn alloc = nullptr;
+  lbm_free_fn release = nullptr;
+  void* user = nullptr;
+  std::vector<Allocation> allocations;
 };
 
 namespace {
@@ -112,6 +146,20 @@ void ctx_free_all(lbm_ctx* ctx) {
   }
   ctx->allocations.clear();
   ctx->device_bytes = 0;
+}
+
+// Sweep record of a prescribed velocity u on face f: u in double and float and
+// 1 / (1 - u.n) in double (n the face's inward normal; |u.n| < 1 is validated).
+lbm::FaceNode face_node(int f, const double* u) {
+  lbm::FaceNode n{};
+  const double un = (f % 2 == 0 ? 1.0 : -1.0) * u[f / 2];
+  for (int j = 0; j < 3; ++j) {
+    n.u[j] = u[j];
+    n.uf[j] = float(u[j]);
+  }
+  n.inv = 1.0 / (1.0 - un);
+  n.pad = 0.0f;
+  return n;
 }
 
 int face_n1(int face, int nx, int ny) { return (face / 2 == 0) ? ny : nx; }
@@ -183,6 +231,13 @@ lbm_status ensure_reduction_buffers(lbm_ctx* ctx) {
   ctx->partials = static_cast<double*>(part);
   ctx->args.snap = snap;
   ctx->args.partials = ctx->partials;
+  return LBM_OK;
+}
+
+// Work of an attached context is issued on its batch's stream: wait for it before the
+// context is used on its own.
+lbm_status settle(lbm_ctx* ctx) {
+  if (ctx->batch) LBM_CUDA(ctx, cudaStreamSynchronize(ctx->batch->stream), "waiting for the context's batch");
   return LBM_OK;
 }
 
@@ -263,16 +318,23 @@ lbm_status lbm_create(int nx, int ny, int nz, double tau, const lbm_face_spec fa
     if (faces[2 * ax].kind == LBM_FACE_PERIODIC) a.periodic |= 1u << ax;
   a.rho0 = rho0;
   a.omega = 1.0 / tau;
+  a.rho0f = float(rho0);
+  a.omegaf = float(1.0 / tau);
+  const double zero[3] = {0.0, 0.0, 0.0};
   for (int f = 0; f < 6; ++f) {
+    const bool vel = faces[f].kind == LBM_FACE_VELOCITY;
     a.face[f].tab = nullptr;
-    for (int j = 0; j < 3; ++j) a.face[f].u[j] = faces[f].kind == LBM_FACE_VELOCITY ? faces[f].u[j] : 0.0;
-    if (faces[f].kind == LBM_FACE_VELOCITY && faces[f].u_table) {
-      const size_t bytes = 3ull * face_n1(f, nx, ny) * face_n2(f, ny, nz) * sizeof(double);
+    a.face[f].uni = face_node(f, vel ? faces[f].u : zero);
+    if (vel && faces[f].u_table) {
+      const size_t m = size_t(face_n1(f, nx, ny)) * face_n2(f, ny, nz);
+      std::vector<lbm::FaceNode> host(m);
+      for (size_t i = 0; i < m; ++i) host[i] = face_node(f, faces[f].u_table + 3 * i);
+      const size_t bytes = m * sizeof(lbm::FaceNode);
       void* t = ctx_alloc(ctx, bytes);
       if (!t) return bail(fail(ctx, LBM_ERR_OOM, "allocation of face table %d failed", f));
-      e = cudaMemcpy(t, faces[f].u_table, bytes, cudaMemcpyHostToDevice);
+      e = cudaMemcpy(t, host.data(), bytes, cudaMemcpyHostToDevice);
       if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "copying a face table"));
-      a.face[f].tab = static_cast<const double*>(t);
+      a.face[f].tab = static_cast<const lbm::FaceNode*>(t);
     }
   }
   e = dispatch_init(ctx, ctx->buf[0]);
@@ -288,6 +350,7 @@ lbm_status lbm_create(int nx, int ny, int nz, double tau, const lbm_face_spec fa
 lbm_status lbm_destroy(lbm_ctx* ctx) {
   if (!ctx) return LBM_OK;
   DeviceGuard g(ctx->device);
+  if (ctx->batch) lbm_batch_detach(ctx->batch, ctx->batch_slot);
   cudaStreamSynchronize(ctx->stream);
   ctx_free_all(ctx);
   delete ctx;
@@ -305,6 +368,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int n) {
   if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0 (got %d)", n);
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, LBM_ERR_CUDA, "cannot make device %d current", ctx->device);
+  if (lbm_status st0 = settle(ctx); st0 != LBM_OK) return st0;
   for (int i = 0; i < n; ++i) {
     ctx->args.src = ctx->buf[ctx->cur];
     ctx->args.dst = ctx->buf[ctx->cur ^ 1];
@@ -321,6 +385,7 @@ lbm_status lbm_step_residual(lbm_ctx* ctx, int n, double* residual, double* mass
   if (n < 1) return fail(ctx, LBM_ERR_ARG, "n must be >= 1 (got %d)", n);
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, LBM_ERR_CUDA, "cannot make device %d current", ctx->device);
+  if (lbm_status st0 = settle(ctx); st0 != LBM_OK) return st0;
   lbm_status st = ensure_reduction_buffers(ctx);
   if (st != LBM_OK) return st;
   st = lbm_step(ctx, n - 1);
@@ -338,6 +403,7 @@ lbm_status lbm_residual(lbm_ctx* ctx, double* residual, double* mass) {
   if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, LBM_ERR_CUDA, "cannot make device %d current", ctx->device);
+  if (lbm_status st0 = settle(ctx); st0 != LBM_OK) return st0;
   lbm_status st = ensure_reduction_buffers(ctx);
   if (st != LBM_OK) return st;
   cudaError_t e;
@@ -356,6 +422,7 @@ lbm_status lbm_macros(lbm_ctx* ctx, void* rho, void* u) {
   if (!rho && !u) return LBM_OK;
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, LBM_ERR_CUDA, "cannot make device %d current", ctx->device);
+  if (lbm_status st0 = settle(ctx); st0 != LBM_OK) return st0;
   cudaError_t e;
   switch (ctx->prec) {
     case LBM_F64: e = lbm::launch_macros<double>(ctx->buf[ctx->cur], ctx->N, ctx->rho0, rho, u, ctx->stream); break;
@@ -374,6 +441,7 @@ static lbm_status copy_populations(lbm_ctx* ctx, void* host_or_dev, int z0, int 
   if (where != LBM_HOST && where != LBM_DEVICE) return fail(ctx, LBM_ERR_ARG, "unknown memory kind %d", int(where));
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, LBM_ERR_CUDA, "cannot make device %d current", ctx->device);
+  if (lbm_status st0 = settle(ctx); st0 != LBM_OK) return st0;
   const size_t es = storage_bytes(ctx->prec);
   const size_t plane = size_t(ctx->nx) * ctx->ny;
   const size_t slab = plane * nzs * es;
@@ -418,6 +486,304 @@ lbm_status lbm_info(const lbm_ctx* ctx, lbm_info_t* out) {
   out->device_bytes = ctx->device_bytes;
   return LBM_OK;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Batches: many resident lattices advanced by one persistent launch per step.
+// ---------------------------------------------------------------------------------
+
+static lbm_status bfail(lbm_batch* b, lbm_status st, const char* msg) {
+  if (b) b->err = msg;
+  g_err = msg;
+  return st;
+}
+
+static lbm_status bcuda(lbm_batch* b, cudaError_t e, const char* what) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  return bfail(b, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, buf);
+}
+
+#define LBM_BCUDA(b, expr, what)                     \
+  do {                                               \
+    cudaError_t e_ = (expr);                         \
+    if (e_ != cudaSuccess) return bcuda(b, e_, what); \
+  } while (0)
+
+static void* batch_alloc(lbm_batch* b, size_t bytes) {
+  void* p = nullptr;
+  if (b->alloc) {
+    p = b->alloc(bytes, b->user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) {
+    b->allocations.push_back({p, bytes});
+    b->device_bytes += int64_t(bytes);
+  }
+  return p;
+}
+
+static void batch_release(lbm_batch* b) {
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  b->graphs.clear();
+  for (lbm_ctx* c : b->slots)
+    if (c) {
+      c->batch = nullptr;
+      c->batch_slot = -1;
+    }
+  for (auto it = b->allocations.rbegin(); it != b->allocations.rend(); ++it) {
+    if (b->release) b->release(it->ptr, b->user);
+    else cudaFree(it->ptr);
+  }
+  b->allocations.clear();
+  if (b->h_hdr) cudaFreeHost(b->h_hdr);
+  if (b->h_ent) cudaFreeHost(b->h_ent);
+  if (b->h_res) cudaFreeHost(b->h_res);
+  if (b->table_free) cudaEventDestroy(b->table_free);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+static cudaError_t batch_launch_sweep(lbm_batch* b, uint32_t parity, bool resid) {
+  switch (b->prec) {
+    case LBM_F64: return lbm::launch_sweep_batched<double>(b->d_hdr, b->d_ent, parity, resid, b->grid, b->stream);
+    case LBM_F32: return lbm::launch_sweep_batched<float>(b->d_hdr, b->d_ent, parity, resid, b->grid, b->stream);
+    default: return lbm::launch_sweep_batched<__half>(b->d_hdr, b->d_ent, parity, resid, b->grid, b->stream);
+  }
+}
+
+// Issue n batched steps (the last with the residual reductions when `resid`).
+static cudaError_t batch_issue(lbm_batch* b, int n, bool resid) {
+  for (int i = 0; i < n; ++i) {
+    cudaError_t e = batch_launch_sweep(b, uint32_t(i & 1), resid && i == n - 1);
+    if (e != cudaSuccess) return e;
+  }
+  if (resid) return lbm::launch_batch_final_reduce(b->d_hdr, b->d_ent, b->capacity, b->d_res, b->stream);
+  return cudaSuccess;
+}
+
+extern "C" {
+
+lbm_status lbm_batch_create(int capacity, lbm_precision prec, lbm_batch** out) {
+  if (!out) return bfail(nullptr, LBM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (capacity < 1 || capacity > (1 << 20)) return bfail(nullptr, LBM_ERR_ARG, "capacity must be in 1 .. 2^20");
+  if (prec < LBM_F64 || prec > LBM_F16_SHIFTED) return bfail(nullptr, LBM_ERR_ARG, "unknown precision");
+  lbm_batch* b = new (std::nothrow) lbm_batch();
+  if (!b) return bfail(nullptr, LBM_ERR_OOM, "host allocation of the batch failed");
+  b->capacity = capacity;
+  b->prec = prec;
+  b->alloc = g_alloc;
+  b->release = g_release;
+  b->user = g_user;
+  auto bail = [&](lbm_status st) {
+    batch_release(b);
+    delete b;
+    return st;
+  };
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e != cudaSuccess) return bail(bcuda(nullptr, e, "cudaGetDevice"));
+  b->slots.assign(capacity, nullptr);
+  b->has_result.assign(capacity, 0);
+  e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return bail(bcuda(nullptr, e, "creating the batch stream"));
+  b->own_stream = true;
+  e = cudaEventCreateWithFlags(&b->table_free, cudaEventDisableTiming);
+  if (e != cudaSuccess) return bail(bcuda(nullptr, e, "creating the table event"));
+  const size_t ent_bytes = sizeof(lbm::BatchEntry) * size_t(capacity);
+  const size_t res_bytes = 4 * sizeof(double) * size_t(capacity);
+  if ((e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_hdr), sizeof(lbm::BatchHeader), cudaHostAllocDefault)) != cudaSuccess ||
+      (e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_ent), ent_bytes, cudaHostAllocDefault)) != cudaSuccess ||
+      (e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_res), res_bytes, cudaHostAllocDefault)) != cudaSuccess)
+    return bail(bcuda(nullptr, e, "pinned host table"));
+  b->d_hdr = static_cast<lbm::BatchHeader*>(batch_alloc(b, sizeof(lbm::BatchHeader)));
+  b->d_ent = static_cast<lbm::BatchEntry*>(batch_alloc(b, ent_bytes));
+  b->d_res = static_cast<double*>(batch_alloc(b, res_bytes));
+  if (!b->d_hdr || !b->d_ent || !b->d_res) return bail(bfail(nullptr, LBM_ERR_OOM, "device allocation of the batch table failed"));
+  memset(b->h_hdr, 0, sizeof(lbm::BatchHeader));
+  e = cudaMemcpy(b->d_hdr, b->h_hdr, sizeof(lbm::BatchHeader), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return bail(bcuda(nullptr, e, "clearing the batch table"));
+  switch (prec) {
+    case LBM_F64: b->grid = lbm::batched_grid<double>(); break;
+    case LBM_F32: b->grid = lbm::batched_grid<float>(); break;
+    default: b->grid = lbm::batched_grid<__half>(); break;
+  }
+  if (b->grid <= 0) return bail(bfail(nullptr, LBM_ERR_CUDA, "occupancy query for the batched sweep failed"));
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return LBM_OK;
+  DeviceGuard g(b->device);
+  batch_release(b);
+  delete b;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set_stream(lbm_batch* b, void* cuda_stream) {
+  if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+  DeviceGuard g(b->device);
+  LBM_BCUDA(b, cudaStreamSynchronize(b->stream), "synchronising the previous stream");
+  for (auto& gr : b->graphs) cudaGraphExecDestroy(gr.exec);
+  b->graphs.clear();
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  b->own_stream = false;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_attach(lbm_batch* b, int slot, lbm_ctx* ctx) {
+  if (!b || !ctx) return bfail(b, LBM_ERR_ARG, "batch or ctx is NULL");
+  if (slot < 0 || slot >= b->capacity) return bfail(b, LBM_ERR_ARG, "slot out of range");
+  if (b->slots[slot]) return bfail(b, LBM_ERR_STATE, "slot is occupied");
+  if (ctx->batch) return bfail(b, LBM_ERR_STATE, "context is attached to a batch already");
+  if (ctx->prec != b->prec) return bfail(b, LBM_ERR_ARG, "context precision differs from the batch's");
+  if (ctx->device != b->device) return bfail(b, LBM_ERR_ARG, "context lives on another device");
+  DeviceGuard g(b->device);
+  lbm_status st = ensure_reduction_buffers(ctx);
+  if (st != LBM_OK) return bfail(b, st, ctx->err.c_str());
+  LBM_BCUDA(b, cudaStreamSynchronize(ctx->stream), "waiting for the context's own work");
+  b->slots[slot] = ctx;
+  b->has_result[slot] = 0;
+  ctx->batch = b;
+  ctx->batch_slot = slot;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_detach(lbm_batch* b, int slot) {
+  if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+  if (slot < 0 || slot >= b->capacity) return bfail(b, LBM_ERR_ARG, "slot out of range");
+  lbm_ctx* ctx = b->slots[slot];
+  if (!ctx) return LBM_OK;
+  DeviceGuard g(b->device);
+  LBM_BCUDA(b, cudaStreamSynchronize(b->stream), "waiting for the batch");
+  b->slots[slot] = nullptr;
+  b->has_result[slot] = 0;
+  ctx->batch = nullptr;
+  ctx->batch_slot = -1;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int n, int residual) {
+  if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+  if (n < 1) return bfail(b, LBM_ERR_ARG, "n must be >= 1");
+  DeviceGuard g(b->device);
+  // the previous upload must have read the host mirror before it is rewritten
+  LBM_BCUDA(b, cudaEventSynchronize(b->table_free), "waiting for the previous table upload");
+  uint32_t nent = 0, blocks = 0;
+  for (int slot = 0; slot < b->capacity; ++slot) {
+    lbm_ctx* c = b->slots[slot];
+    if (!c) continue;
+    lbm::BatchEntry& e = b->h_ent[nent++];
+    e.a = c->args;
+    e.buf[0] = c->buf[0];
+    e.buf[1] = c->buf[1];
+    e.cur = uint32_t(c->cur);
+    e.block_begin = blocks;
+    e.nblocks = lbm::sweep_blocks(c->N);
+    e.slot = uint32_t(slot);
+    blocks += e.nblocks;
+  }
+  b->h_hdr->nentries = nent;
+  b->h_hdr->total_blocks = blocks;
+  b->total_blocks = blocks;
+  if (nent == 0) return LBM_OK;
+  const bool resid = residual != 0;
+  LBM_BCUDA(b, cudaMemcpyAsync(b->d_hdr, b->h_hdr, sizeof(lbm::BatchHeader), cudaMemcpyHostToDevice, b->stream),
+            "uploading the batch header");
+  LBM_BCUDA(b, cudaMemcpyAsync(b->d_ent, b->h_ent, sizeof(lbm::BatchEntry) * nent, cudaMemcpyHostToDevice, b->stream),
+            "uploading the batch table");
+  LBM_BCUDA(b, cudaEventRecord(b->table_free, b->stream), "recording the table event");
+  if (b->stream) {
+    // the n-step loop as one CUDA graph; its kernels read the table from device memory,
+    // so one graph per (n, residual) serves every membership of the batch
+    cudaGraphExec_t exec = nullptr;
+    for (auto& gr : b->graphs)
+      if (gr.n == n && gr.resid == resid) exec = gr.exec;
+    if (!exec) {
+      cudaGraph_t graph = nullptr;
+      LBM_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "beginning graph capture");
+      cudaError_t e = batch_issue(b, n, resid);
+      cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+      if (e != cudaSuccess) return bcuda(b, e, "capturing the batched steps");
+      if (e2 != cudaSuccess) return bcuda(b, e2, "ending graph capture");
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return bcuda(b, e, "instantiating the step graph");
+      if (b->graphs.size() >= 8) {
+        cudaGraphExecDestroy(b->graphs.front().exec);
+        b->graphs.erase(b->graphs.begin());
+      }
+      b->graphs.push_back({n, resid, exec});
+    }
+    LBM_BCUDA(b, cudaGraphLaunch(exec, b->stream), "launching the step graph");
+  } else {
+    LBM_BCUDA(b, batch_issue(b, n, resid), "batched step launch");
+  }
+  if (resid)
+    LBM_BCUDA(b, cudaMemcpyAsync(b->h_res, b->d_res, 4 * sizeof(double) * b->capacity, cudaMemcpyDeviceToHost, b->stream),
+              "reading the batch results");
+  b->results_valid = resid;
+  for (int slot = 0; slot < b->capacity; ++slot) {
+    lbm_ctx* c = b->slots[slot];
+    b->has_result[slot] = (c && resid) ? 1 : 0;
+    if (!c) continue;
+    c->cur ^= (n & 1);
+    c->steps += n;
+  }
+  b->steps += n;
+  b->launches += n + (resid ? 1 : 0);
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_results(lbm_batch* b, double* residual, double* mass, int* status) {
+  if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+  DeviceGuard g(b->device);
+  LBM_BCUDA(b, cudaStreamSynchronize(b->stream), "waiting for the batch");
+  for (int slot = 0; slot < b->capacity; ++slot) {
+    double r = NAN, m = NAN;
+    int st = 1;  // no result for this slot
+    if (b->results_valid && b->has_result[slot]) {
+      const double* h = b->h_res + 4 * slot;
+      r = h[2] > 0.0 ? std::sqrt(h[1]) / std::sqrt(h[2]) : std::sqrt(h[1]);
+      m = h[0];
+      st = (h[3] != 0.0 || !std::isfinite(h[0]) || !std::isfinite(r)) ? int(LBM_ERR_DIVERGED) : int(LBM_OK);
+    }
+    if (residual) residual[slot] = r;
+    if (mass) mass[slot] = m;
+    if (status) status[slot] = st;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_info(const lbm_batch* b, lbm_batch_info_t* out) {
+  if (!b || !out) return bfail(nullptr, LBM_ERR_ARG, "batch or out is NULL");
+  int attached = 0;
+  int64_t nodes = 0;
+  for (lbm_ctx* c : b->slots)
+    if (c) {
+      ++attached;
+      nodes += c->N;
+    }
+  out->capacity = b->capacity;
+  out->attached = attached;
+  out->grid = b->grid;
+  out->nodes = nodes;
+  out->steps = b->steps;
+  out->kernel_launches = b->launches;
+  out->device_bytes = b->device_bytes;
+  return LBM_OK;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"
+
+extern "C" {
 
 const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
 
