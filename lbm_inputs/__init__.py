@@ -9,7 +9,9 @@ This module holds no lattice-Boltzmann arithmetic. It only defines
 
 Face numbering: 0: x=0, 1: x=nx-1, 2: y=0, 3: y=ny-1, 4: z=0, 5: z=nz-1. A velocity
 face carries a float64 table of shape (n2, n1, 3) over its two tangential axes in
-increasing axis order (x faces: [z][y], y faces: [z][x], z faces: [y][x]).
+increasing axis order (x faces: [z][y], y faces: [z][x], z faces: [y][x]); a pressure
+face carries a density table (n2, n1) and a velocity table whose tangential part is the
+prescribed tangential velocity.
 """
 from __future__ import annotations
 
@@ -20,6 +22,7 @@ import numpy as np
 
 PERIODIC = 0
 VELOCITY = 1
+PRESSURE = 2
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
 
@@ -77,6 +80,7 @@ class Workload:
     rho0: float = 1.0
     steps: int = 0
     meta: dict = field(default_factory=dict)
+    ptabs: list = field(default_factory=lambda: [None] * 6)
 
     @property
     def cells(self) -> int:
@@ -87,23 +91,33 @@ class Workload:
         return self.nx, self.ny, self.nz
 
 
-def make_workload(name, nx, ny, nz, tau, face_u, steps=0, rho0=1.0, meta=None) -> Workload:
-    """``face_u[i]`` is None (periodic), a 3-vector (uniform) or a (n2, n1, 3) table."""
-    kinds, tabs = [], []
+def make_workload(name, nx, ny, nz, tau, face_u, steps=0, rho0=1.0, meta=None, face_p=None) -> Workload:
+    """``face_u[i]`` is None (periodic), a 3-vector (uniform) or a (n2, n1, 3) table;
+    ``face_p[i]``, when given, makes face i a pressure face with that density (a scalar
+    or an (n2, n1) table) and face_u[i] its tangential velocity (zero if None)."""
+    face_p = face_p or [None] * 6
+    kinds, tabs, ptabs = [], [], []
     for i in range(6):
-        fu = face_u[i]
-        if fu is None:
+        fu, fp = face_u[i], face_p[i]
+        if fu is None and fp is None:
             kinds.append(PERIODIC)
             tabs.append(None)
+            ptabs.append(None)
             continue
-        kinds.append(VELOCITY)
-        arr = np.asarray(fu, np.float64)
+        kinds.append(PRESSURE if fp is not None else VELOCITY)
+        arr = np.asarray(fu if fu is not None else ZERO, np.float64)
         if arr.shape == (3,):
             arr = uniform_table(i, nx, ny, nz, arr)
         if arr.shape != face_shape(i, nx, ny, nz) + (3,):
             raise ValueError(f"face {i}: table shape {arr.shape}")
         tabs.append(np.ascontiguousarray(arr))
-    return Workload(name, nx, ny, nz, tau, tuple(kinds), tabs, rho0, steps, meta or {})
+        if fp is None:
+            ptabs.append(None)
+        else:
+            pt = np.empty(face_shape(i, nx, ny, nz))
+            pt[...] = np.asarray(fp, np.float64)
+            ptabs.append(pt)
+    return Workload(name, nx, ny, nz, tau, tuple(kinds), tabs, rho0, steps, meta or {}, ptabs)
 
 
 ZERO = (0.0, 0.0, 0.0)
@@ -142,6 +156,15 @@ def poiseuille(lz=32, tau=1.0, peak=0.02, lx=4, ly=4, steps=0) -> Workload:
     tab = np.stack([prof, np.zeros_like(prof), np.zeros_like(prof)], axis=-1)
     return make_workload("poiseuille", lx, ly, lz, tau, [tab, tab, None, None, ZERO, ZERO], steps,
                          meta={"peak": peak})
+
+
+def pressure_duct(n=16, length=48, tau=1.0, rho_in=1.005, rho_out=0.995, steps=0) -> Workload:
+    """Pressure-driven square duct: n x n cross-section with resting walls on the y and
+    z faces (walls on the end nodes, width n-1), density rho_in at x=0 and rho_out at
+    x=length-1, no tangential velocity on the pressure planes."""
+    return make_workload("pressure_duct", length, n, n, tau, [None, None, ZERO, ZERO, ZERO, ZERO], steps,
+                         meta={"rho_in": rho_in, "rho_out": rho_out},
+                         face_p=[rho_in, rho_out, None, None, None, None])
 
 
 def random_face_workload(seed: int, nx: int, ny: int, nz: int, tau: float, periodic=(False, False, False),

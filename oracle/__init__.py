@@ -35,20 +35,21 @@ def lib():
         L.orc_moments.argtypes = [_dp, _dp]
         L.orc_collide.argtypes = [_dp, C.c_double]
         L.orc_close_face.argtypes = [C.c_int, C.c_int, _dp, _dp, C.POINTER(C.c_double)]
-        L.orc_close_edge.argtypes = [C.c_int, C.c_int, _dp]
-        L.orc_close_corner.argtypes = [C.c_int, C.c_int, C.c_int, _dp]
+        L.orc_close_edge.argtypes = [C.c_int, C.c_int, _dp, C.c_double]
+        L.orc_close_corner.argtypes = [C.c_int, C.c_int, C.c_int, _dp, C.c_double]
+        L.orc_close_face_pressure.argtypes = [C.c_int, C.c_int, _dp, C.c_double, _dp, C.POINTER(C.c_double)]
         L.orc_stream.argtypes = [C.c_int] * 3 + [_ip, _dp, _dp]
-        L.orc_step.argtypes = [C.c_int] * 3 + [_ip, C.c_void_p, C.c_double, _dp, _dp, C.c_int]
-        L.orc_run.argtypes = [C.c_int] * 3 + [_ip, C.c_void_p, C.c_double, C.c_int, _dp, _dp, C.c_int]
+        L.orc_step.argtypes = [C.c_int] * 3 + [_ip, C.c_void_p, C.c_void_p, C.c_double, _dp, _dp, C.c_int]
+        L.orc_run.argtypes = [C.c_int] * 3 + [_ip, C.c_void_p, C.c_void_p, C.c_double, C.c_int, _dp, _dp, C.c_int]
         L.orc_init_equilibrium.argtypes = [C.c_int] * 3 + [C.c_double, _dp]
         L.orc_macros.argtypes = [C.c_int] * 3 + [_dp, _dp, _dp]
         L.orc_reduce.argtypes = [C.c_int] * 3 + [_dp, C.c_void_p, _dp]
         L.orc_sources.argtypes = [C.c_int] * 3 + [_ip, C.c_int64, _lp, _lp]
-        L.orc_update_gathered.argtypes = [C.c_int] * 3 + [_ip, C.c_void_p, C.c_double, C.c_int64,
+        L.orc_update_gathered.argtypes = [C.c_int] * 3 + [_ip, C.c_void_p, C.c_void_p, C.c_double, C.c_int64,
                                                           _lp, _dp, _dp, C.c_int]
         L.orc_lattice.argtypes = [_ip, _dp, _ip]
         L.orc_threads.restype = C.c_int
-        for name in ("orc_close_face", "orc_close_edge", "orc_close_corner", "orc_stream",
+        for name in ("orc_close_face", "orc_close_edge", "orc_close_corner", "orc_close_face_pressure", "orc_stream",
                      "orc_step", "orc_run", "orc_sources", "orc_update_gathered"):
             getattr(L, name).restype = C.c_int
         _LIB = L
@@ -96,31 +97,47 @@ def close_face(face: int, f, u, form: int = 0):
     return g, rho.value
 
 
-def close_edge(face_a: int, face_b: int, f) -> np.ndarray:
+def close_face_pressure(face: int, f, rho0: float, u_t, form: int = 0):
+    """Pressure closure of one node: density rho0 and tangential velocity u_t (normal
+    component ignored) prescribed; returns (closed populations, normal velocity)."""
     g = np.array(f, np.float64)
-    _check(lib().orc_close_edge(face_a, face_b, g), "close_edge")
+    vn = C.c_double()
+    _check(lib().orc_close_face_pressure(face, form, g, float(rho0), np.ascontiguousarray(u_t, np.float64),
+                                         C.byref(vn)), "close_face_pressure")
+    return g, vn.value
+
+
+def close_edge(face_a: int, face_b: int, f, rho_p: float = -1.0) -> np.ndarray:
+    """No-slip edge; rho_p > 0 when the edge borders a pressure plane of that density."""
+    g = np.array(f, np.float64)
+    _check(lib().orc_close_edge(face_a, face_b, g, float(rho_p)), "close_edge")
     return g
 
 
-def close_corner(face_x: int, face_y: int, face_z: int, f) -> np.ndarray:
+def close_corner(face_x: int, face_y: int, face_z: int, f, rho_p: float = -1.0) -> np.ndarray:
+    """No-slip corner; rho_p > 0 when the corner borders a pressure plane."""
     g = np.array(f, np.float64)
-    _check(lib().orc_close_corner(face_x, face_y, face_z, g), "close_corner")
+    _check(lib().orc_close_corner(face_x, face_y, face_z, g, float(rho_p)), "close_corner")
     return g
 
 
 class Lattice:
-    """A lattice description for the oracle: dims, face kinds and velocity tables.
+    """A lattice description for the oracle: dims, face kinds and boundary tables.
 
-    ``utabs[i]`` is a float64 array of shape (n2, n1, 3) for a velocity face, over the
-    face's two tangential axes in increasing axis order, or None for a periodic face.
+    ``kinds[i]``: 0 periodic, 1 velocity, 2 pressure. ``utabs[i]`` is a float64 array of
+    shape (n2, n1, 3) over the face's two tangential axes in increasing axis order (the
+    prescribed velocity; for a pressure face its tangential part), or None for a
+    periodic face. ``ptabs[i]`` is the (n2, n1) prescribed density of a pressure face.
     """
 
-    def __init__(self, nx, ny, nz, kinds, utabs, tau):
+    def __init__(self, nx, ny, nz, kinds, utabs, tau, ptabs=None):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.kinds = np.ascontiguousarray(kinds, np.int32)
         self.tau = float(tau)
         self._tabs = []
         ptrs = (C.c_void_p * 6)()
+        pptrs = (C.c_void_p * 6)()
+        ptabs = ptabs if ptabs is not None else [None] * 6
         for i in range(6):
             t = utabs[i]
             if t is None:
@@ -128,11 +145,16 @@ class Lattice:
             t = np.ascontiguousarray(t, np.float64)
             self._tabs.append(t)
             ptrs[i] = t.ctypes.data
+            if ptabs[i] is not None:
+                pt = np.ascontiguousarray(ptabs[i], np.float64)
+                self._tabs.append(pt)
+                pptrs[i] = pt.ctypes.data
         self._ptrs = ptrs
+        self._pptrs = pptrs
 
     @classmethod
     def from_workload(cls, wl):
-        return cls(wl.nx, wl.ny, wl.nz, wl.kinds, wl.utabs, wl.tau)
+        return cls(wl.nx, wl.ny, wl.nz, wl.kinds, wl.utabs, wl.tau, getattr(wl, "ptabs", None))
 
     @property
     def shape(self):
@@ -162,14 +184,14 @@ def stream(lat: Lattice, f) -> np.ndarray:
 def step(lat: Lattice, f, form: int = 0) -> np.ndarray:
     fin = np.ascontiguousarray(f, np.float64)
     out = np.zeros(lat.shape)
-    _check(lib().orc_step(*lat.dims(), lat.kinds, lat._ptrs, lat.tau, fin, out, form), "step")
+    _check(lib().orc_step(*lat.dims(), lat.kinds, lat._ptrs, lat._pptrs, lat.tau, fin, out, form), "step")
     return out
 
 
 def run(lat: Lattice, f, nsteps: int, form: int = 0) -> np.ndarray:
     g = np.array(f, np.float64, order="C")
     work = np.empty_like(g)
-    _check(lib().orc_run(*lat.dims(), lat.kinds, lat._ptrs, lat.tau, int(nsteps), g, work, form),
+    _check(lib().orc_run(*lat.dims(), lat.kinds, lat._ptrs, lat._pptrs, lat.tau, int(nsteps), g, work, form),
            "run")
     return g
 
@@ -208,8 +230,8 @@ def update_gathered(lat: Lattice, nodes, gathered, form: int = 0) -> np.ndarray:
     nodes = np.ascontiguousarray(nodes, np.int64)
     g = np.ascontiguousarray(gathered, np.float64).reshape(len(nodes), Q)
     out = np.zeros_like(g)
-    _check(lib().orc_update_gathered(*lat.dims(), lat.kinds, lat._ptrs, lat.tau, len(nodes), nodes,
-                                     g, out, form), "update_gathered")
+    _check(lib().orc_update_gathered(*lat.dims(), lat.kinds, lat._ptrs, lat._pptrs, lat.tau, len(nodes),
+                                     nodes, g, out, form), "update_gathered")
     return out
 
 

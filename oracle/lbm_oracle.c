@@ -15,10 +15,13 @@
  *   - lattice arrays are [19][nz][ny][nx] with x fastest;
  *   - faces: 0: x=0, 1: x=nx-1, 2: y=0, 3: y=ny-1, 4: z=0, 5: z=nz-1; a face's
  *     inward normal is +e_a for the low face and -e_a for the high face of axis a;
- *   - a velocity face carries a table of prescribed velocities [n2][n1][3], where
- *     (t1, t2) are the two tangential axes in increasing axis order;
- *   - an axis is periodic when both of its faces are periodic (kind 0), otherwise
- *     both of its faces carry the velocity condition (kind 1); v = 0 is no-slip;
+ *   - a velocity face (kind 1) carries a table of prescribed velocities [n2][n1][3],
+ *     where (t1, t2) are the two tangential axes in increasing axis order; v = 0 is
+ *     no-slip. A pressure face (kind 2) carries a density table [n2][n1] and a velocity
+ *     table whose tangential part is prescribed (its normal part is ignored);
+ *   - an axis is periodic when both of its faces are periodic (kind 0); otherwise each
+ *     of its faces is a velocity or a pressure face. Pressure faces lie on one axis at
+ *     most, so an edge or corner borders at most one pressure plane;
  *   - every sum over populations runs in index order i = 1..19.
  *
  * Readings of the paper where it is ambiguous or garbled (all other steps follow the
@@ -39,6 +42,11 @@
  *      edges" when the in/outflow profile decays to zero there).
  *   R6 a time step is: pull streaming, boundary closure on the unknown populations,
  *      then BGK collision; the initial state counts as post-collision.
+ *   R7 appendix, back plane: the velocity form of the density relation is printed
+ *      for v_x; the back plane's normal velocity is v_y.
+ *   R8 pressure planes: edges and corners next to one take the buried-link values
+ *      that make their density the prescribed one (eq. buried_rho, corner variant);
+ *      the along-edge momentum correction is the same as for velocity planes.
  */
 #include <math.h>
 #include <stdint.h>
@@ -119,13 +127,14 @@ void orc_collide(double* f, double tau) {
 
 /* ----------------------------------------------------------------------------------
  * Face closure, form (i): the explicit per-plane formulas. Each returns rho and
- * overwrites the five unknown populations; v is the prescribed velocity in lattice
- * axes.
+ * overwrites the five unknown populations; v is the velocity of the node in lattice
+ * axes. rho_fixed > 0 is a density given in advance (the pressure variant); otherwise
+ * rho comes from the plane's density relation.
  * -------------------------------------------------------------------------------- */
 
 /* Bottom plane z = 0: eq. uin, eq. f5, eq. f9-f17, eq. Nx, eq. Ny. */
-static double close_bottom(double* f, const double* v) {
-  double rho = (F(1) + F(2) + F(3) + F(4) + F(7) + F(8) + F(11) + F(12) + F(19) +
+static double close_bottom(double* f, const double* v, double rho_fixed) {
+  double rho = rho_fixed > 0.0 ? rho_fixed : (F(1) + F(2) + F(3) + F(4) + F(7) + F(8) + F(11) + F(12) + F(19) +
                 2.0 * (F(6) + F(10) + F(14) + F(16) + F(18))) / (1.0 - v[2]);
   double Nx = 0.5 * (F(1) + F(7) + F(8) - (F(2) + F(11) + F(12))) - rho * v[0] / 3.0;
   double Ny = 0.5 * (F(3) + F(7) + F(11) - (F(4) + F(8) + F(12))) - rho * v[1] / 3.0;
@@ -138,8 +147,8 @@ static double close_bottom(double* f, const double* v) {
 }
 
 /* Top plane z = nz-1: appendix, top plane. */
-static double close_top(double* f, const double* v) {
-  double rho = (F(1) + F(2) + F(3) + F(4) + F(7) + F(11) + F(12) + F(8) + F(19) +
+static double close_top(double* f, const double* v, double rho_fixed) {
+  double rho = rho_fixed > 0.0 ? rho_fixed : (F(1) + F(2) + F(3) + F(4) + F(7) + F(11) + F(12) + F(8) + F(19) +
                 2.0 * (F(5) + F(9) + F(13) + F(15) + F(17))) / (v[2] + 1.0);
   double Nx = 0.5 * (F(1) + F(7) + F(8) - (F(2) + F(11) + F(12))) - rho * v[0] / 3.0;
   double Ny = 0.5 * (F(3) + F(7) + F(11) - (F(4) + F(8) + F(12))) - rho * v[1] / 3.0;
@@ -152,8 +161,8 @@ static double close_top(double* f, const double* v) {
 }
 
 /* Left plane x = 0: appendix, eq. rhooutx, eq. Nxy, eq. Nxz. */
-static double close_left(double* f, const double* v) {
-  double rho = (F(3) + F(4) + F(5) + F(6) + F(15) + F(16) + F(17) + F(18) + F(19) +
+static double close_left(double* f, const double* v, double rho_fixed) {
+  double rho = rho_fixed > 0.0 ? rho_fixed : (F(3) + F(4) + F(5) + F(6) + F(15) + F(16) + F(17) + F(18) + F(19) +
                 2.0 * (F(2) + F(11) + F(12) + F(13) + F(14))) / (1.0 - v[0]);
   double Ny = 0.5 * (F(3) + F(15) + F(16) - (F(4) + F(17) + F(18))) - rho * v[1] / 3.0;
   double Nz = 0.5 * (F(5) + F(17) + F(15) - (F(6) + F(16) + F(18))) - rho * v[2] / 3.0;
@@ -166,8 +175,8 @@ static double close_left(double* f, const double* v) {
 }
 
 /* Right plane x = nx-1: appendix, eq. rhoinx. */
-static double close_right(double* f, const double* v) {
-  double rho = (F(3) + F(4) + F(5) + F(6) + F(15) + F(16) + F(17) + F(18) + F(19) +
+static double close_right(double* f, const double* v, double rho_fixed) {
+  double rho = rho_fixed > 0.0 ? rho_fixed : (F(3) + F(4) + F(5) + F(6) + F(15) + F(16) + F(17) + F(18) + F(19) +
                 2.0 * (F(1) + F(7) + F(8) + F(9) + F(10))) / (v[0] + 1.0);
   double Ny = 0.5 * (F(3) + F(15) + F(16) - (F(4) + F(17) + F(18))) - rho * v[1] / 3.0;
   double Nz = 0.5 * (F(5) + F(17) + F(15) - (F(6) + F(16) + F(18))) - rho * v[2] / 3.0;
@@ -180,8 +189,8 @@ static double close_right(double* f, const double* v) {
 }
 
 /* Front plane y = 0: appendix, eq. rhoiny, eq. Nyx, eq. Nyz. */
-static double close_front(double* f, const double* v) {
-  double rho = (F(1) + F(2) + F(5) + F(6) + F(9) + F(10) + F(13) + F(14) + F(19) +
+static double close_front(double* f, const double* v, double rho_fixed) {
+  double rho = rho_fixed > 0.0 ? rho_fixed : (F(1) + F(2) + F(5) + F(6) + F(9) + F(10) + F(13) + F(14) + F(19) +
                 2.0 * (F(4) + F(8) + F(12) + F(17) + F(18))) / (1.0 - v[1]);
   double Nx = 0.5 * (F(1) + F(9) + F(10) - (F(2) + F(13) + F(14))) - rho * v[0] / 3.0;
   double Nz = 0.5 * (F(5) + F(9) + F(13) - (F(6) + F(10) + F(14))) - rho * v[2] / 3.0;
@@ -195,8 +204,8 @@ static double close_front(double* f, const double* v) {
 
 /* Back plane y = ny-1: appendix, eq. rhoouty (velocity form; the printed v_x of the
  * density-given variant is read as v_y, which this velocity form does not use). */
-static double close_back(double* f, const double* v) {
-  double rho = (F(1) + F(2) + F(5) + F(6) + F(9) + F(10) + F(13) + F(14) + F(19) +
+static double close_back(double* f, const double* v, double rho_fixed) {
+  double rho = rho_fixed > 0.0 ? rho_fixed : (F(1) + F(2) + F(5) + F(6) + F(9) + F(10) + F(13) + F(14) + F(19) +
                 2.0 * (F(3) + F(7) + F(11) + F(15) + F(16))) / (v[1] + 1.0);
   double Nx = 0.5 * (F(1) + F(9) + F(10) - (F(2) + F(13) + F(14))) - rho * v[0] / 3.0;
   double Nz = 0.5 * (F(5) + F(9) + F(13) - (F(6) + F(10) + F(14))) - rho * v[2] / 3.0;
@@ -215,7 +224,7 @@ static double close_back(double* f, const double* v) {
  *   f_-i = f_i - 6 w_i rho c_i.v - (rho/3) t_i.v + 1/2 sum_j f_j (t_i.c_j)(1 - |c_j.n|)
  * with t_i = c_i - (c_i.n) n and rho from the plane's density relation (eq. uin).
  * -------------------------------------------------------------------------------- */
-static double close_face_compact(double* f, int face, const double* v) {
+static double close_face_compact(double* f, int face, const double* v, double rho_fixed) {
   int n[3];
   face_normal(face, n);
   /* density: in-plane populations once, outgoing ones twice, unknown ones not at all */
@@ -226,7 +235,7 @@ static double close_face_compact(double* f, int face, const double* v) {
     else if (cn < 0) s += 2.0 * f[k];
   }
   double vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
-  double rho = s / (1.0 - vn);
+  double rho = rho_fixed > 0.0 ? rho_fixed : s / (1.0 - vn);
   for (int k = 0; k < Q; ++k) {
     int cn = dot_ci(k, n);
     if (cn >= 0) continue; /* only outgoing i */
@@ -244,23 +253,80 @@ static double close_face_compact(double* f, int face, const double* v) {
   return rho;
 }
 
+static double close_face_form(int face, int form, double* f, const double* v, double rho_fixed) {
+  if (form == 1) return close_face_compact(f, face, v, rho_fixed);
+  switch (face) {
+    case 0: return close_left(f, v, rho_fixed);
+    case 1: return close_right(f, v, rho_fixed);
+    case 2: return close_front(f, v, rho_fixed);
+    case 3: return close_back(f, v, rho_fixed);
+    case 4: return close_bottom(f, v, rho_fixed);
+    default: return close_top(f, v, rho_fixed);
+  }
+}
+
 /* Entry for both forms: form 0 = explicit per-plane formulas, form 1 = compact rule. */
 int orc_close_face(int face, int form, double* f, const double* v, double* rho_out) {
-  double rho;
   if (face < 0 || face > 5) return ORC_ERR_ARG;
-  if (form == 1) {
-    rho = close_face_compact(f, face, v);
-  } else {
-    switch (face) {
-      case 0: rho = close_left(f, v); break;
-      case 1: rho = close_right(f, v); break;
-      case 2: rho = close_front(f, v); break;
-      case 3: rho = close_back(f, v); break;
-      case 4: rho = close_bottom(f, v); break;
-      default: rho = close_top(f, v); break;
-    }
-  }
+  double rho = close_face_form(face, form, f, v, -1.0);
   if (rho_out) *rho_out = rho;
+  return ORC_OK;
+}
+
+/* ----------------------------------------------------------------------------------
+ * Pressure (density) variant of the face closure (Sec. "General on-site velocity
+ * boundary condition", eq. rhoin; appendix: top plane, eq. voutx, eq. uinx, eq. uiny,
+ * eq. uouty). The density rho0 and the tangential velocity are prescribed; the normal
+ * velocity follows from the plane's density relation; the unknown populations then
+ * follow the same rules as for the velocity closure with rho = rho0.
+ * -------------------------------------------------------------------------------- */
+
+/* Velocity component along the plane's axis, explicit per-plane relations (form 0). */
+static double pressure_velocity_explicit(int face, const double* f, double rho0) {
+  switch (face) {
+    case 4: /* bottom, eq. rhoin */
+      return 1.0 - (F(1) + F(2) + F(3) + F(4) + F(7) + F(8) + F(11) + F(12) + F(19) +
+                    2.0 * (F(6) + F(10) + F(14) + F(16) + F(18))) / rho0;
+    case 5: /* top */
+      return -1.0 + (F(1) + F(2) + F(3) + F(4) + F(7) + F(11) + F(12) + F(8) + F(19) +
+                     2.0 * (F(5) + F(9) + F(13) + F(15) + F(17))) / rho0;
+    case 0: /* left, eq. voutx */
+      return 1.0 - (F(3) + F(4) + F(5) + F(6) + F(15) + F(16) + F(17) + F(18) + F(19) +
+                    2.0 * (F(2) + F(11) + F(12) + F(13) + F(14))) / rho0;
+    case 1: /* right, eq. uinx */
+      return -1.0 + (F(3) + F(4) + F(5) + F(6) + F(15) + F(16) + F(17) + F(18) + F(19) +
+                     2.0 * (F(1) + F(7) + F(8) + F(9) + F(10))) / rho0;
+    case 2: /* front, eq. uiny */
+      return 1.0 - (F(1) + F(2) + F(5) + F(6) + F(9) + F(10) + F(13) + F(14) + F(19) +
+                    2.0 * (F(4) + F(8) + F(12) + F(17) + F(18))) / rho0;
+    default: /* back, eq. uouty (its printed v_x read as v_y) */
+      return -1.0 + (F(1) + F(2) + F(5) + F(6) + F(9) + F(10) + F(13) + F(14) + F(19) +
+                     2.0 * (F(3) + F(7) + F(11) + F(15) + F(16))) / rho0;
+  }
+}
+
+/* Same from the general relation u.n = 1 - (sum in-plane + 2 sum outgoing) / rho0 (form 1). */
+static double pressure_velocity_compact(int face, const double* f, double rho0) {
+  int n[3];
+  face_normal(face, n);
+  double s = 0.0;
+  for (int k = 0; k < Q; ++k) {
+    int cn = dot_ci(k, n);
+    if (cn == 0) s += f[k];
+    else if (cn < 0) s += 2.0 * f[k];
+  }
+  return (double)n[face / 2] * (1.0 - s / rho0);
+}
+
+/* Pressure closure: v holds the tangential velocity (its normal component is ignored);
+ * the normal component found is returned in *vn_out (along the plane's axis). */
+int orc_close_face_pressure(int face, int form, double* f, double rho0, const double* v, double* vn_out) {
+  if (face < 0 || face > 5 || !(rho0 > 0.0)) return ORC_ERR_ARG;
+  double u[3] = {v[0], v[1], v[2]};
+  double vn = form == 1 ? pressure_velocity_compact(face, f, rho0) : pressure_velocity_explicit(face, f, rho0);
+  u[face / 2] = vn;
+  close_face_form(face, form, f, u, rho0);
+  if (vn_out) *vn_out = vn;
   return ORC_OK;
 }
 
@@ -269,7 +335,7 @@ int orc_close_face(int face, int form, double* f, const double* v, double* rho_o
  * eq. edge, eq. buried; readings R2, R3). n1, n2 are the inward normals of the
  * two planes meeting at the edge.
  * -------------------------------------------------------------------------------- */
-static void close_edge_normals(double* f, const int n1[3], const int n2[3]) {
+static void close_edge_normals(double* f, const int n1[3], const int n2[3], double rho_p) {
   int e[3] = {n1[1] * n2[2] - n1[2] * n2[1], n1[2] * n2[0] - n1[0] * n2[2],
               n1[0] * n2[1] - n1[1] * n2[0]};
   int buried[Q], unknown[Q];
@@ -295,29 +361,32 @@ static void close_edge_normals(double* f, const int n1[3], const int n2[3]) {
   Ne *= 0.25;
   for (int k = 0; k < Q; ++k)
     if (unknown[k] && !buried[k]) f[k] -= dot_ci(k, e) * Ne;
-  /* 3. buried links and rest population (eq. buried) */
+  /* 3. buried links and rest population (eq. buried); next to a pressure plane the
+   *    node density is the prescribed rho_p (eq. buried_rho) */
   double s = 0.0;
   for (int k = 0; k < Q - 1; ++k)
     if (!buried[k]) s += f[k];
   double fb = s / 22.0;
+  if (rho_p > 0.0) fb = (rho_p - 22.0 * fb) / 14.0;
   for (int k = 0; k < Q - 1; ++k)
     if (buried[k]) f[k] = fb;
   F(19) = 12.0 * fb;
 }
 
-int orc_close_edge(int face_a, int face_b, double* f) {
+/* rho_p > 0: the edge borders a pressure plane of density rho_p. */
+int orc_close_edge(int face_a, int face_b, double* f, double rho_p) {
   if (face_a < 0 || face_a > 5 || face_b < 0 || face_b > 5 || face_a / 2 == face_b / 2) return ORC_ERR_ARG;
   int n1[3], n2[3];
   face_normal(face_a, n1);
   face_normal(face_b, n2);
-  close_edge_normals(f, n1, n2);
+  close_edge_normals(f, n1, n2, rho_p);
   return ORC_OK;
 }
 
 /* ----------------------------------------------------------------------------------
  * Corner, no-slip (eq. corner, reading R4).
  * -------------------------------------------------------------------------------- */
-static void close_corner_normals(double* f, const int n1[3], const int n2[3], const int n3[3]) {
+static void close_corner_normals(double* f, const int n1[3], const int n2[3], const int n3[3], double rho_p) {
   int s3[3] = {n1[0] + n2[0] + n3[0], n1[1] + n2[1] + n3[1], n1[2] + n2[2] + n3[2]};
   int buried[Q], unknown[Q];
   for (int k = 0; k < Q; ++k) {
@@ -330,18 +399,20 @@ static void close_corner_normals(double* f, const int n1[3], const int n2[3], co
   for (int k = 0; k < Q - 1; ++k)
     if (!buried[k]) s += f[k];
   double fb = s / 18.0;
+  if (rho_p > 0.0) fb = rho_p / 18.0 - fb; /* next to a pressure plane */
   for (int k = 0; k < Q - 1; ++k)
     if (buried[k]) f[k] = fb;
   F(19) = 12.0 * fb;
 }
 
-int orc_close_corner(int face_x, int face_y, int face_z, double* f) {
+/* rho_p > 0: the corner borders a pressure plane of density rho_p. */
+int orc_close_corner(int face_x, int face_y, int face_z, double* f, double rho_p) {
   if (face_x < 0 || face_x > 1 || face_y < 2 || face_y > 3 || face_z < 4 || face_z > 5) return ORC_ERR_ARG;
   int n1[3], n2[3], n3[3];
   face_normal(face_x, n1);
   face_normal(face_y, n2);
   face_normal(face_z, n3);
-  close_corner_normals(f, n1, n2, n3);
+  close_corner_normals(f, n1, n2, n3, rho_p);
   return ORC_OK;
 }
 
@@ -350,8 +421,10 @@ int orc_close_corner(int face_x, int face_y, int face_z, double* f) {
  * -------------------------------------------------------------------------------- */
 typedef struct {
   int nx, ny, nz;
-  int kind[6];            /* 0 periodic, 1 velocity */
-  const double* utab[6];  /* [n2][n1][3] per velocity face */
+  int kind[6];            /* 0 periodic, 1 velocity, 2 pressure */
+  const double* utab[6];  /* [n2][n1][3] per velocity or pressure face (pressure: the
+                             tangential velocity; the normal component is ignored) */
+  const double* ptab[6];  /* [n2][n1] prescribed density per pressure face */
   double tau;
 } lattice_t;
 
@@ -360,13 +433,21 @@ static int axis_periodic(const lattice_t* L, int a) { return L->kind[2 * a] == 0
 
 static int lattice_check(const lattice_t* L) {
   if (L->nx < 1 || L->ny < 1 || L->nz < 1) return ORC_ERR_ARG;
+  int pressure_axes = 0;
   for (int a = 0; a < 3; ++a) {
-    if (L->kind[2 * a] != L->kind[2 * a + 1]) return ORC_ERR_ARG; /* periodic faces come in pairs */
-    if (L->kind[2 * a] != 0 && L->kind[2 * a] != 1) return ORC_ERR_ARG;
-    if (L->kind[2 * a] == 1 && axis_dim(L, a) < 3) return ORC_ERR_ARG;
-    if (L->kind[2 * a] == 1 && (!L->utab[2 * a] || !L->utab[2 * a + 1])) return ORC_ERR_ARG;
+    for (int s = 0; s < 2; ++s) {
+      int k = L->kind[2 * a + s];
+      if (k < 0 || k > 2) return ORC_ERR_ARG;
+      if (k != 0 && !L->utab[2 * a + s]) return ORC_ERR_ARG;
+      if (k == 2 && !L->ptab[2 * a + s]) return ORC_ERR_ARG;
+    }
+    /* periodic faces come in pairs */
+    if ((L->kind[2 * a] == 0) != (L->kind[2 * a + 1] == 0)) return ORC_ERR_ARG;
+    if (L->kind[2 * a] != 0 && axis_dim(L, a) < 3) return ORC_ERR_ARG;
+    if (L->kind[2 * a] == 2 || L->kind[2 * a + 1] == 2) ++pressure_axes;
   }
-  return ORC_OK;
+  /* an edge or corner borders at most one pressure plane */
+  return pressure_axes <= 1 ? ORC_OK : ORC_ERR_ARG;
 }
 
 /* Linear index of the node that population k at (x,y,z) is pulled from, i.e.
@@ -384,12 +465,11 @@ static int64_t pull_source(const lattice_t* L, int x, int y, int z, int k) {
   return ((int64_t)p[2] * L->ny + p[1]) * L->nx + p[0];
 }
 
-/* Prescribed velocity at (x,y,z) on face `face` (tangential axes in increasing order). */
-static const double* face_velocity(const lattice_t* L, int face, int x, int y, int z) {
+/* Table position of node (x,y,z) on face `face` (tangential axes in increasing order). */
+static int64_t face_index(const lattice_t* L, int face, int x, int y, int z) {
   int c[3] = {x, y, z};
   int a = face / 2, t1 = (a == 0) ? 1 : 0, t2 = (a == 2) ? 1 : 2;
-  int n1 = axis_dim(L, t1);
-  return L->utab[face] + 3 * ((int64_t)c[t2] * n1 + c[t1]);
+  return (int64_t)c[t2] * axis_dim(L, t1) + c[t1];
 }
 
 /* Boundary closure and collision of one node whose streamed populations are in f
@@ -397,24 +477,31 @@ static const double* face_velocity(const lattice_t* L, int face, int x, int y, i
 static int update_node(const lattice_t* L, int x, int y, int z, double* f, int form) {
   int c[3] = {x, y, z};
   int faces[3], nf = 0;
+  double rho_p = -1.0; /* density of a bordering pressure plane, if any */
   for (int a = 0; a < 3; ++a) {
     if (axis_periodic(L, a)) continue;
-    if (c[a] == 0) faces[nf++] = 2 * a;
-    else if (c[a] == axis_dim(L, a) - 1) faces[nf++] = 2 * a + 1;
+    int fc = -1;
+    if (c[a] == 0) fc = 2 * a;
+    else if (c[a] == axis_dim(L, a) - 1) fc = 2 * a + 1;
+    if (fc < 0) continue;
+    faces[nf++] = fc;
+    if (L->kind[fc] == 2) rho_p = L->ptab[fc][face_index(L, fc, x, y, z)];
   }
   if (nf == 1) {
-    orc_close_face(faces[0], form, f, face_velocity(L, faces[0], x, y, z), NULL);
+    const double* u = L->utab[faces[0]] + 3 * face_index(L, faces[0], x, y, z);
+    if (L->kind[faces[0]] == 2) orc_close_face_pressure(faces[0], form, f, rho_p, u, NULL);
+    else close_face_form(faces[0], form, f, u, -1.0);
   } else if (nf == 2) {
     int n1[3], n2[3];
     face_normal(faces[0], n1);
     face_normal(faces[1], n2);
-    close_edge_normals(f, n1, n2);
+    close_edge_normals(f, n1, n2, rho_p);
   } else if (nf == 3) {
     int n1[3], n2[3], n3[3];
     face_normal(faces[0], n1);
     face_normal(faces[1], n2);
     face_normal(faces[2], n3);
-    close_corner_normals(f, n1, n2, n3);
+    close_corner_normals(f, n1, n2, n3, rho_p);
   }
   for (int k = 0; k < Q; ++k)
     if (isnan(f[k])) return ORC_ERR_UNFILLED;
@@ -422,12 +509,13 @@ static int update_node(const lattice_t* L, int x, int y, int z, double* f, int f
   return ORC_OK;
 }
 
-static int make_lattice(lattice_t* L, int nx, int ny, int nz, const int* kind,
-                        const double* const* utab, double tau) {
+static int make_lattice(lattice_t* L, int nx, int ny, int nz, const int* kind, const double* const* utab,
+                        const double* const* ptab, double tau) {
   L->nx = nx; L->ny = ny; L->nz = nz; L->tau = tau;
   for (int i = 0; i < 6; ++i) {
     L->kind[i] = kind[i];
     L->utab[i] = utab ? utab[i] : NULL;
+    L->ptab[i] = ptab ? ptab[i] : NULL;
   }
   return lattice_check(L);
 }
@@ -435,10 +523,9 @@ static int make_lattice(lattice_t* L, int nx, int ny, int nz, const int* kind,
 /* Pull streaming only: out[k][node] = in[k][node - c_k], NaN where unknown. */
 int orc_stream(int nx, int ny, int nz, const int* kind, const double* fin, double* fout) {
   lattice_t L;
-  const double* none[6] = {0, 0, 0, 0, 0, 0};
   double dummy = 0.0;
-  for (int i = 0; i < 6; ++i) none[i] = &dummy; /* tables unused by streaming */
-  int rc = make_lattice(&L, nx, ny, nz, kind, none, 1.0);
+  const double* none[6] = {&dummy, &dummy, &dummy, &dummy, &dummy, &dummy}; /* tables unused by streaming */
+  int rc = make_lattice(&L, nx, ny, nz, kind, none, none, 1.0);
   if (rc) return rc;
   int64_t N = (int64_t)nx * ny * nz;
   for (int z = 0; z < nz; ++z)
@@ -454,10 +541,10 @@ int orc_stream(int nx, int ny, int nz, const int* kind, const double* fin, doubl
 }
 
 /* One time step fin -> fout (streaming, closure, collision). */
-int orc_step(int nx, int ny, int nz, const int* kind, const double* const* utab, double tau,
-             const double* fin, double* fout, int form) {
+int orc_step(int nx, int ny, int nz, const int* kind, const double* const* utab, const double* const* ptab,
+             double tau, const double* fin, double* fout, int form) {
   lattice_t L;
-  int rc = make_lattice(&L, nx, ny, nz, kind, utab, tau);
+  int rc = make_lattice(&L, nx, ny, nz, kind, utab, ptab, tau);
   if (rc) return rc;
   int64_t N = (int64_t)nx * ny * nz;
   int err = 0;
@@ -480,12 +567,12 @@ int orc_step(int nx, int ny, int nz, const int* kind, const double* const* utab,
 
 /* nsteps time steps; f holds the initial and the final state, work is scratch of the
  * same size. */
-int orc_run(int nx, int ny, int nz, const int* kind, const double* const* utab, double tau,
-            int nsteps, double* f, double* work, int form) {
+int orc_run(int nx, int ny, int nz, const int* kind, const double* const* utab, const double* const* ptab,
+            double tau, int nsteps, double* f, double* work, int form) {
   int64_t n = (int64_t)Q * nx * ny * nz;
   double *a = f, *b = work;
   for (int s = 0; s < nsteps; ++s) {
-    int rc = orc_step(nx, ny, nz, kind, utab, tau, a, b, form);
+    int rc = orc_step(nx, ny, nz, kind, utab, ptab, tau, a, b, form);
     if (rc) return rc;
     double* t = a; a = b; b = t;
   }
@@ -542,7 +629,7 @@ int orc_sources(int nx, int ny, int nz, const int* kind, int64_t n, const int64_
   lattice_t L;
   double dummy = 0.0;
   const double* none[6] = {&dummy, &dummy, &dummy, &dummy, &dummy, &dummy};
-  int rc = make_lattice(&L, nx, ny, nz, kind, none, 1.0);
+  int rc = make_lattice(&L, nx, ny, nz, kind, none, none, 1.0);
   if (rc) return rc;
   int64_t N = (int64_t)nx * ny * nz;
   for (int64_t i = 0; i < n; ++i) {
@@ -560,10 +647,10 @@ int orc_sources(int nx, int ny, int nz, const int* kind, int64_t n, const int64_
 /* Closure and collision of listed nodes from their streamed populations
  * (g[i*19 + k], NaN where unknown); results in out[i*19 + k]. */
 int orc_update_gathered(int nx, int ny, int nz, const int* kind, const double* const* utab,
-                        double tau, int64_t n, const int64_t* nodes, const double* g,
-                        double* out, int form) {
+                        const double* const* ptab, double tau, int64_t n, const int64_t* nodes,
+                        const double* g, double* out, int form) {
   lattice_t L;
-  int rc = make_lattice(&L, nx, ny, nz, kind, utab, tau);
+  int rc = make_lattice(&L, nx, ny, nz, kind, utab, ptab, tau);
   if (rc) return rc;
   int64_t N = (int64_t)nx * ny * nz;
   for (int64_t i = 0; i < n; ++i) {
