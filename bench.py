@@ -234,15 +234,47 @@ def whole_job_mlups(world: int, nodes: int, steps: int, max_ms: float) -> float:
     return world * nodes * steps / (max_ms * 1e-3) / 1e6
 
 
-def run_variant(wl, precision, steps, warmup, resid_every, dist_ctx):
+# GB300's FP64 pipe: NVIDIA's 1.25 TFLOP/s FP64 figure is 2 DFMA per SM per clock at
+# 152 SMs and 2.07 GHz, i.e. 2 FP64 instructions per SM per clock.
+FP64_INST_PER_SM_CLOCK = 2.0
+
+
+def profiled_fp64_per_node(wl_name: str):
+    """FP64 instructions per node update of the FP64 sweep from the committed ncu
+    counters, if they were taken on the current sweep source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh)[f"sweep/f64/{wl_name}"]
+    except Exception:  # noqa: BLE001
+        return None
+    return rec.get("fp64_inst_per_node") if rec.get("source_sha") == sweep_source_hash() else None
+
+
+def run_variant(wl, precision, steps, warmup, resid_every, dist_ctx, clocks=None):
+    import torch
+
     import paper_0811_4593_gb300 as lbm
     with lbm.Lattice.from_workload(wl, precision) as lat:
         total_ms, step_ms, launches, _ = measure(lat, steps, warmup, resid_every, dist_ctx)
     hbm, _ = measured_hbm_peak()
     ach = BYTES_PER_UPDATE[precision] * wl.cells / (step_ms * 1e-3) / 1e9
-    return {"mlups": wl.cells * steps / (total_ms * 1e-3) / 1e6, "ms_per_step": total_ms / steps,
-            "sweep_ms": step_ms, "achieved_gbs": ach, "frac": ach / hbm, "steps": steps,
-            "bytes_per_update": BYTES_PER_UPDATE[precision]}
+    out = {"mlups": wl.cells * steps / (total_ms * 1e-3) / 1e6, "ms_per_step": total_ms / steps,
+           "sweep_ms": step_ms, "achieved_gbs": ach, "frac": ach / hbm, "steps": steps,
+           "bytes_per_update": BYTES_PER_UPDATE[precision]}
+    if precision == "f64":
+        # the FP64 sweep is bound by the FP64 pipe, not by HBM
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        peak = FP64_INST_PER_SM_CLOCK * sms * mhz * 1e6 / 1e9
+        per_node = profiled_fp64_per_node("channel256")
+        alu = {"bound": "alu", "unit": "G FP64 inst/s", "peak": round(peak, 1),
+               "peak_basis": f"{FP64_INST_PER_SM_CLOCK:g} FP64 inst / SM / clock x {sms} SMs x {mhz:g} MHz",
+               "fp64_inst_per_node": per_node}
+        if per_node:
+            a = per_node * wl.cells / (step_ms * 1e-3) / 1e9
+            alu.update(achieved=round(a, 1), frac=round(a / peak, 4))
+        out["roofline"] = alu
+    return out
 
 
 def e2e_run(wl, precision, steps, resid_every, dist_ctx):
@@ -340,7 +372,7 @@ def native(args):
         vs = {}
         for p in ("f16", "f64"):
             if p != args.precision:
-                vs[p] = run_variant(wl, p, args.variant_steps, 20, args.resid_every, d)
+                vs[p] = run_variant(wl, p, args.variant_steps, 20, args.resid_every, d, clock)
                 torch.cuda.empty_cache()
         out["variants"] = vs
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:

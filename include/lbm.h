@@ -62,19 +62,28 @@ typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16_SHIFTED = 2 } lbm_precision;
 /* Periodic faces wrap streaming to the opposite face (periodic boundaries of the
  * paper's Sec. "Boundary conditions") and must come in pairs. A velocity face applies
  * the on-site velocity condition; a prescribed velocity of zero is the on-site
- * no-slip wall (Sec. "On-site no-slip boundary condition"). */
-typedef enum { LBM_FACE_PERIODIC = 0, LBM_FACE_VELOCITY = 1 } lbm_face_kind;
+ * no-slip wall (Sec. "On-site no-slip boundary condition"). A pressure face applies
+ * the density variant (eq. rhoin and its appendix analogues): the density and the
+ * tangential velocity are prescribed and the normal velocity follows from the plane's
+ * density relation; edges and corners next to it take the buried-link values that give
+ * them the prescribed density (eq. buried_rho and the corner variant). */
+typedef enum { LBM_FACE_PERIODIC = 0, LBM_FACE_VELOCITY = 1, LBM_FACE_PRESSURE = 2 } lbm_face_kind;
 
 typedef enum { LBM_HOST = 0, LBM_DEVICE = 1 } lbm_memory;
 
 typedef struct {
   int kind;              /* lbm_face_kind */
   double u[3];           /* prescribed velocity (lattice units) on every node of the face,
-                            used when u_table is NULL */
+                            used when u_table is NULL; on a pressure face only its
+                            tangential components are used */
   const double* u_table; /* optional HOST array [n2][n1][3] of prescribed velocities, one
                             per node of the face plane, over the face's two tangential
                             axes in increasing axis order (x faces [z][y], y faces [z][x],
                             z faces [y][x]); copied by lbm_create, not retained */
+  double rho;            /* pressure face: prescribed density on every node, used when
+                            rho_table is NULL */
+  const double* rho_table; /* pressure face: optional HOST array [n2][n1] of prescribed
+                              densities, laid out like u_table; copied, not retained */
 } lbm_face_spec;
 
 /* Device allocator hook: every device buffer the library owns is obtained through
@@ -91,9 +100,10 @@ LBM_API lbm_status lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, vo
  *  rho0  initial density; the initial state is the post-collision state
  *        f_i = f_i^eq(rho0, 0) (eq. feq).
  * Validation (LBM_ERR_ARG): tau > 1/2; every dimension >= 3; 19 * nx*ny*nz < 2^32;
- * periodic faces in pairs; |u.n| < 1 on every velocity face node. On edges and
- * corners (nodes on two or three velocity faces) the no-slip rules of Sec. "On-site
- * no-slip boundary condition" apply and the face tables are not read there.
+ * periodic faces in pairs; |u.n| < 1 on every velocity face node; finite positive
+ * densities on pressure faces, which may lie on one axis only. On edges and corners
+ * (nodes on two or three non-periodic faces) the no-slip rules of Sec. "On-site
+ * no-slip boundary condition" apply and velocity tables are not read there.
  * Ownership: *out is owned by the library until lbm_destroy. */
 LBM_API lbm_status lbm_create(int nx, int ny, int nz, double tau, const lbm_face_spec faces[6],
                       lbm_precision prec, double rho0, lbm_ctx** out);

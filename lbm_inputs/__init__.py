@@ -167,6 +167,28 @@ def pressure_duct(n=16, length=48, tau=1.0, rho_in=1.005, rho_out=0.995, steps=0
                          face_p=[rho_in, rho_out, None, None, None, None])
 
 
+def random_pressure_workload(seed: int, nx: int, ny: int, nz: int, tau: float, periodic_y: bool = False,
+                             amp: float = 0.02) -> Workload:
+    """Pressure faces at x=0 and x=nx-1 with random densities 1 +- amp and random
+    tangential velocities; random velocity tables on the y and z faces (y periodic on
+    request)."""
+    face_u, face_p = [], []
+    for i in range(6):
+        if i in (2, 3) and periodic_y:
+            face_u.append(None)
+            face_p.append(None)
+            continue
+        n2, n1 = face_shape(i, nx, ny, nz)
+        r = uniform(seed, 200 + i, np.arange(n2 * n1 * 3)).reshape(n2, n1, 3)
+        face_u.append(0.04 * (2.0 * r - 1.0))
+        if i < 2:
+            q = uniform(seed, 210 + i, np.arange(n2 * n1)).reshape(n2, n1)
+            face_p.append(1.0 + amp * (2.0 * q - 1.0))
+        else:
+            face_p.append(None)
+    return make_workload(f"random_pressure{seed}", nx, ny, nz, tau, face_u, face_p=face_p)
+
+
 def random_face_workload(seed: int, nx: int, ny: int, nz: int, tau: float, periodic=(False, False, False),
                          amp: float = 0.05) -> Workload:
     """Random velocity tables on every walled face (for boundary-rule checks)."""

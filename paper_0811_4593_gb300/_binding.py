@@ -20,7 +20,7 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_STATE 
 PRECISIONS = {"f64": 0, "f32": 1, "f16": 2}
 STORAGE_DTYPE = {"f64": np.float64, "f32": np.float32, "f16": np.float16}
 LBM_HOST, LBM_DEVICE = 0, 1
-FACE_PERIODIC, FACE_VELOCITY = 0, 1
+FACE_PERIODIC, FACE_VELOCITY, FACE_PRESSURE = 0, 1, 2
 
 # Every function the header declares, with its C signature.
 EXPORTS = {
@@ -53,7 +53,17 @@ EXPORTS = {
 
 
 class FaceSpec(C.Structure):
-    _fields_ = [("kind", C.c_int), ("u", C.c_double * 3), ("u_table", C.POINTER(C.c_double))]
+    _fields_ = [("kind", C.c_int), ("u", C.c_double * 3), ("u_table", C.POINTER(C.c_double)),
+                ("rho", C.c_double), ("rho_table", C.POINTER(C.c_double))]
+
+
+class Pressure:
+    """A pressure face: prescribed density (scalar or (n2, n1) table) and tangential
+    velocity (3-vector or (n2, n1, 3) table; its normal component is ignored)."""
+
+    def __init__(self, rho, u=(0.0, 0.0, 0.0)):
+        self.rho = rho
+        self.u = u
 
 
 class Info(C.Structure):
@@ -142,25 +152,39 @@ def use_default_allocator():
 
 
 def _face_specs(nx, ny, nz, faces):
-    """faces[i]: None (periodic), a 3-vector (uniform) or an (n2, n1, 3) table."""
+    """faces[i]: None (periodic), a velocity 3-vector or (n2, n1, 3) table, or a
+    Pressure."""
     specs = (FaceSpec * 6)()
     keep = []
+    dims = (nx, ny, nz)
     for i, fu in enumerate(faces):
         if fu is None:
             specs[i].kind = FACE_PERIODIC
             continue
-        specs[i].kind = FACE_VELOCITY
+        a = i // 2
+        t1, t2 = [b for b in range(3) if b != a]
+        shape2 = (dims[t2], dims[t1])
+        if isinstance(fu, Pressure):
+            specs[i].kind = FACE_PRESSURE
+            rho = np.asarray(fu.rho, np.float64)
+            if rho.shape == ():
+                specs[i].rho = float(rho)
+            else:
+                if rho.shape != shape2:
+                    raise ValueError(f"face {i}: density table shape {rho.shape}, expected {shape2}")
+                rho = np.ascontiguousarray(rho)
+                keep.append(rho)
+                specs[i].rho_table = rho.ctypes.data_as(C.POINTER(C.c_double))
+            fu = fu.u
+        else:
+            specs[i].kind = FACE_VELOCITY
         arr = np.asarray(fu, np.float64)
         if arr.shape == (3,):
             for j in range(3):
                 specs[i].u[j] = float(arr[j])
-            specs[i].u_table = None
         else:
-            a = i // 2
-            t1, t2 = [b for b in range(3) if b != a]
-            dims = (nx, ny, nz)
-            if arr.shape != (dims[t2], dims[t1], 3):
-                raise ValueError(f"face {i}: table shape {arr.shape}, expected {(dims[t2], dims[t1], 3)}")
+            if arr.shape != shape2 + (3,):
+                raise ValueError(f"face {i}: table shape {arr.shape}, expected {shape2 + (3,)}")
             arr = np.ascontiguousarray(arr)
             keep.append(arr)
             specs[i].u_table = arr.ctypes.data_as(C.POINTER(C.c_double))
@@ -171,7 +195,8 @@ class Lattice:
     """One D3Q19 lattice resident on the current CUDA device.
 
     ``faces`` lists the six faces (x=0, x=nx-1, y=0, y=ny-1, z=0, z=nz-1); each is None
-    (periodic), a velocity 3-vector, or a table of prescribed velocities (n2, n1, 3).
+    (periodic), a velocity 3-vector, a table of prescribed velocities (n2, n1, 3), or a
+    Pressure (prescribed density and tangential velocity).
     ``precision`` is "f64" (f stored as double), "f32" or "f16" (f - w rho0 stored as
     float or binary16).
     """
@@ -199,7 +224,17 @@ class Lattice:
 
     @classmethod
     def from_workload(cls, wl, precision="f32", **kw):
-        faces = [None if k == FACE_PERIODIC else t for k, t in zip(wl.kinds, wl.utabs)]
+        """A lattice for any object with nx, ny, nz, tau, rho0, kinds, utabs (and ptabs
+        for pressure faces)."""
+        ptabs = getattr(wl, "ptabs", None) or [None] * 6
+        faces = []
+        for k, t, p in zip(wl.kinds, wl.utabs, ptabs):
+            if k == FACE_PERIODIC:
+                faces.append(None)
+            elif k == FACE_PRESSURE:
+                faces.append(Pressure(p, t))
+            else:
+                faces.append(t)
         return cls(wl.nx, wl.ny, wl.nz, wl.tau, faces, precision, wl.rho0, **kw)
 
     # -- lifetime -------------------------------------------------------------------

@@ -74,25 +74,21 @@ struct FaceVals {
   double inv;
 };
 
-// On-site velocity closure of a plane with inward normal SG * e_A: density from the
-// in-plane populations and twice the outgoing ones (eq. uin and the appendix
-// relations), transverse corrections N on the two tangential axes (eqs. Nx, Ny and
-// analogues), and for every unknown population i (c_i.n > 0)
-//   h_i = h_-i + 6 w_i rho c_i.u - t_i.N     (eq. f5, eqs. f9-f17, appendix).
-// The density is formed in double: rho = (rho0 + S) / (1 - u.n), where S, the
-// relation's sum over the shifted populations (its weights sum to 1), is exact in
-// double (accumulated in double for FP64, as an error-free float pair otherwise).
+// The relation's sum over the shifted populations of a plane with inward normal
+// SG * e_A: in-plane populations once, outgoing ones twice (its weights sum to 1, so
+// the plane's density relation reads rho (1 - u.n) = ref + S). Exact in double:
+// accumulated in double for FP64, as an error-free float pair otherwise.
 template <int A, int SG, typename T>
-__device__ __forceinline__ void close_face(T (&h)[Q], const FaceVals<T>& fv, double rho0) {
-  double S;
+__device__ __forceinline__ double relation_sum(const T (&h)[Q]) {
   if constexpr (std::is_same<T, double>::value) {
-    S = 0.0;
+    double S = 0.0;
     static_for<0, Q>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
       constexpr int cn = SG * ca(k, A);
       if constexpr (cn == 0) S += h[k];
       else if constexpr (cn < 0) S += 2.0 * h[k];
     });
+    return S;
   } else {
     float hi = 0.0f, lo = 0.0f;
     static_for<0, Q>([&](auto kc) {
@@ -101,9 +97,16 @@ __device__ __forceinline__ void close_face(T (&h)[Q], const FaceVals<T>& fv, dou
       if constexpr (cn == 0) two_sum_acc(hi, lo, h[k]);
       else if constexpr (cn < 0) two_sum_acc(hi, lo, __fmul_rn(2.0f, h[k]));
     });
-    S = double(hi) + double(lo);
+    return double(hi) + double(lo);
   }
-  const T rho = T((rho0 + S) * fv.inv);
+}
+
+// Unknown populations of a plane with inward normal SG * e_A, given the node's density
+// rho and velocity u: transverse corrections N on the two tangential axes (eqs. Nx, Ny
+// and analogues) and, for every unknown i (c_i.n > 0),
+//   h_i = h_-i + 6 w_i rho c_i.u - t_i.N     (eq. f5, eqs. f9-f17, appendix).
+template <int A, int SG, typename T>
+__device__ __forceinline__ void fill_unknowns(T (&h)[Q], T rho, const T (&u)[3]) {
   constexpr int B = (A == 0) ? 1 : 0;
   constexpr int C = (A == 2) ? 1 : 2;
   T sb = T(0), sc = T(0);
@@ -115,13 +118,13 @@ __device__ __forceinline__ void close_face(T (&h)[Q], const FaceVals<T>& fv, dou
     }
   });
   const T third = T(1) / T(3);
-  const T NB = T(0.5) * sb - rho * fv.u[B] * third;
-  const T NC = T(0.5) * sc - rho * fv.u[C] * third;
+  const T NB = T(0.5) * sb - rho * u[B] * third;
+  const T NC = T(0.5) * sc - rho * u[C] * third;
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     if constexpr (SG * ca(k, A) > 0) {
       constexpr int m = opp(k);
-      const T cu = T(cx(k)) * fv.u[0] + T(cy(k)) * fv.u[1] + T(cz(k)) * fv.u[2];
+      const T cu = T(cx(k)) * u[0] + T(cy(k)) * u[1] + T(cz(k)) * u[2];
       const T coef = T(6 * w36(k)) / T(36);
       T t = T(0);
       if constexpr (ca(k, B) != 0) t += T(ca(k, B)) * NB;
@@ -129,6 +132,27 @@ __device__ __forceinline__ void close_face(T (&h)[Q], const FaceVals<T>& fv, dou
       h[k] = h[m] + coef * rho * cu - t;
     }
   });
+}
+
+// On-site velocity closure (eq. uin and the appendix relations): the density
+// rho = (ref + S) / (1 - u.n), formed in double (fv.inv = 1 / (1 - u.n) from the host),
+// then the unknown populations.
+template <int A, int SG, typename T>
+__device__ __forceinline__ void close_face(T (&h)[Q], const FaceVals<T>& fv, double ref) {
+  const T rho = T((ref + relation_sum<A, SG>(h)) * fv.inv);
+  fill_unknowns<A, SG>(h, rho, fv.u);
+}
+
+// Pressure variant (eq. rhoin and the appendix relations): the density rho_p
+// (fv.inv) and the tangential velocity are prescribed; the normal velocity
+// u.n = 1 - (ref + S) / rho_p, formed in double; then the unknown populations.
+template <int A, int SG, typename T>
+__device__ __forceinline__ void close_face_pressure(T (&h)[Q], const FaceVals<T>& fv, double ref) {
+  const double rho_p = fv.inv;
+  const double un = 1.0 - (ref + relation_sum<A, SG>(h)) / rho_p;
+  T u[3] = {fv.u[0], fv.u[1], fv.u[2]};
+  u[A] = T(double(SG) * un);
+  fill_unknowns<A, SG>(h, T(rho_p), u);
 }
 
 // Concave no-slip edge of the planes with inward normals n1 = S1 e_A1 and
@@ -151,8 +175,11 @@ struct EdgeRule {
   __host__ __device__ static constexpr int along(int k) { return cx(k) * ex + cy(k) * ey + cz(k) * ez; }
 };
 
+// Next to a pressure plane (pressure = true) the buried links and the rest population
+// instead make the node density the prescribed one (eq. buried_rho): with drho_p the
+// prescribed density minus the reference, buried = (drho_p - sum of the 16) / 14.
 template <int A1, int S1, int A2, int S2, typename T>
-__device__ __forceinline__ void close_edge(T (&h)[Q]) {
+__device__ __forceinline__ void close_edge(T (&h)[Q], bool pressure, T drho_p) {
   using R = EdgeRule<A1, S1, A2, S2>;
   static_assert(R::PE >= 0 && R::ME >= 0, "edge direction must be a lattice vector");
   static_for<0, Q>([&](auto kc) {
@@ -171,7 +198,7 @@ __device__ __forceinline__ void close_edge(T (&h)[Q]) {
     constexpr int k = decltype(kc)::value;
     if constexpr (!R::buried(k)) s += h[k];
   });
-  const T fb = s / T(22);
+  const T fb = pressure ? (drho_p - s) / T(14) : s / T(22);
   static_for<0, Q - 1>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     if constexpr (R::buried(k)) h[k] = fb;
@@ -193,8 +220,10 @@ struct CornerRule {
   }
 };
 
+// Next to a pressure plane: buried = (drho_p - sum of the 12) / 18 (the corner variant,
+// prescribed density rho_p, drho_p = rho_p - reference).
 template <int SX, int SY, int SZ, typename T>
-__device__ __forceinline__ void close_corner(T (&h)[Q]) {
+__device__ __forceinline__ void close_corner(T (&h)[Q], bool pressure, T drho_p) {
   using R = CornerRule<SX, SY, SZ>;
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
@@ -206,7 +235,7 @@ __device__ __forceinline__ void close_corner(T (&h)[Q]) {
     constexpr int k = decltype(kc)::value;
     if constexpr (!R::buried(k)) s += h[k];
   });
-  const T fb = s / T(18);
+  const T fb = pressure ? (drho_p - s) / T(18) : s / T(18);
   static_for<0, Q - 1>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     if constexpr (R::buried(k)) h[k] = fb;
@@ -255,11 +284,46 @@ __device__ __forceinline__ FaceVals<T> face_values(const SweepArgs& a, uint32_t 
   return v;
 }
 
+// Reference density of the register values: 0 for FP64 (unshifted), rho0 otherwise.
+template <typename T>
+__device__ __forceinline__ double ref_density(const SweepArgs& a) {
+  return std::is_same<T, double>::value ? 0.0 : a.rho0;
+}
+
+template <int A, int SG>
+constexpr int face_id() { return 2 * A + (SG > 0 ? 0 : 1); }
+
 template <int A, int SG, typename T>
 __device__ __forceinline__ void face_case(const SweepArgs& a, uint32_t x, uint32_t y, uint32_t z, T (&h)[Q]) {
-  // reference density of the register values: 0 for FP64 (unshifted), rho0 otherwise
-  const double ref = std::is_same<T, double>::value ? 0.0 : a.rho0;
-  close_face<A, SG>(h, face_values<A, SG, T>(a, x, y, z), ref);
+  const FaceVals<T> fv = face_values<A, SG, T>(a, x, y, z);
+  if (a.pressure & (1u << face_id<A, SG>())) close_face_pressure<A, SG>(h, fv, ref_density<T>(a));
+  else close_face<A, SG>(h, fv, ref_density<T>(a));
+}
+
+// Edge of faces (A1, S1) and (A2, S2); when one of them is a pressure face its density
+// at the node fixes the node's density.
+template <int A1, int S1, int A2, int S2, typename T>
+__device__ __forceinline__ void edge_case(const SweepArgs& a, uint32_t x, uint32_t y, uint32_t z, T (&h)[Q]) {
+  constexpr uint32_t b1 = 1u << face_id<A1, S1>(), b2 = 1u << face_id<A2, S2>();
+  if (a.pressure & (b1 | b2)) {
+    const double rp = (a.pressure & b1) ? face_values<A1, S1, T>(a, x, y, z).inv : face_values<A2, S2, T>(a, x, y, z).inv;
+    close_edge<A1, S1, A2, S2>(h, true, T(rp - ref_density<T>(a)));
+  } else {
+    close_edge<A1, S1, A2, S2>(h, false, T(0));
+  }
+}
+
+template <int SX, int SY, int SZ, typename T>
+__device__ __forceinline__ void corner_case(const SweepArgs& a, uint32_t x, uint32_t y, uint32_t z, T (&h)[Q]) {
+  constexpr uint32_t bx = 1u << face_id<0, SX>(), by = 1u << face_id<1, SY>(), bz = 1u << face_id<2, SZ>();
+  if (a.pressure & (bx | by | bz)) {
+    const double rp = (a.pressure & bx)   ? face_values<0, SX, T>(a, x, y, z).inv
+                      : (a.pressure & by) ? face_values<1, SY, T>(a, x, y, z).inv
+                                          : face_values<2, SZ, T>(a, x, y, z).inv;
+    close_corner<SX, SY, SZ>(h, true, T(rp - ref_density<T>(a)));
+  } else {
+    close_corner<SX, SY, SZ>(h, false, T(0));
+  }
 }
 
 // code = fx + 3 fy + 9 fz with f = 0 (interior or periodic), 1 (low face), 2 (high face)
@@ -275,29 +339,29 @@ __device__ __forceinline__ void apply_boundary(int code, const SweepArgs& a, uin
     case 9: face_case<2, +1>(a, x, y, z, h); break;
     case 18: face_case<2, -1>(a, x, y, z, h); break;
     // x-y edges
-    case 4: close_edge<0, +1, 1, +1>(h); break;
-    case 5: close_edge<0, -1, 1, +1>(h); break;
-    case 7: close_edge<0, +1, 1, -1>(h); break;
-    case 8: close_edge<0, -1, 1, -1>(h); break;
+    case 4: edge_case<0, +1, 1, +1>(a, x, y, z, h); break;
+    case 5: edge_case<0, -1, 1, +1>(a, x, y, z, h); break;
+    case 7: edge_case<0, +1, 1, -1>(a, x, y, z, h); break;
+    case 8: edge_case<0, -1, 1, -1>(a, x, y, z, h); break;
     // x-z edges
-    case 10: close_edge<0, +1, 2, +1>(h); break;
-    case 11: close_edge<0, -1, 2, +1>(h); break;
-    case 19: close_edge<0, +1, 2, -1>(h); break;
-    case 20: close_edge<0, -1, 2, -1>(h); break;
+    case 10: edge_case<0, +1, 2, +1>(a, x, y, z, h); break;
+    case 11: edge_case<0, -1, 2, +1>(a, x, y, z, h); break;
+    case 19: edge_case<0, +1, 2, -1>(a, x, y, z, h); break;
+    case 20: edge_case<0, -1, 2, -1>(a, x, y, z, h); break;
     // y-z edges
-    case 12: close_edge<1, +1, 2, +1>(h); break;
-    case 15: close_edge<1, -1, 2, +1>(h); break;
-    case 21: close_edge<1, +1, 2, -1>(h); break;
-    case 24: close_edge<1, -1, 2, -1>(h); break;
+    case 12: edge_case<1, +1, 2, +1>(a, x, y, z, h); break;
+    case 15: edge_case<1, -1, 2, +1>(a, x, y, z, h); break;
+    case 21: edge_case<1, +1, 2, -1>(a, x, y, z, h); break;
+    case 24: edge_case<1, -1, 2, -1>(a, x, y, z, h); break;
     // corners
-    case 13: close_corner<+1, +1, +1>(h); break;
-    case 14: close_corner<-1, +1, +1>(h); break;
-    case 16: close_corner<+1, -1, +1>(h); break;
-    case 17: close_corner<-1, -1, +1>(h); break;
-    case 22: close_corner<+1, +1, -1>(h); break;
-    case 23: close_corner<-1, +1, -1>(h); break;
-    case 25: close_corner<+1, -1, -1>(h); break;
-    case 26: close_corner<-1, -1, -1>(h); break;
+    case 13: corner_case<+1, +1, +1>(a, x, y, z, h); break;
+    case 14: corner_case<-1, +1, +1>(a, x, y, z, h); break;
+    case 16: corner_case<+1, -1, +1>(a, x, y, z, h); break;
+    case 17: corner_case<-1, -1, +1>(a, x, y, z, h); break;
+    case 22: corner_case<+1, +1, -1>(a, x, y, z, h); break;
+    case 23: corner_case<-1, +1, -1>(a, x, y, z, h); break;
+    case 25: corner_case<+1, -1, -1>(a, x, y, z, h); break;
+    case 26: corner_case<-1, -1, -1>(a, x, y, z, h); break;
     default: break;
   }
 }
@@ -438,8 +502,6 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
     const uint32_t yp = (y + 1 < a.ny) ? y + 1 : (py ? 0 : a.ny - 1);
     const uint32_t zm = z ? z - 1 : (pz ? a.nz - 1 : 0);
     const uint32_t zp = (z + 1 < a.nz) ? z + 1 : (pz ? 0 : a.nz - 1);
-    const S* __restrict__ src = static_cast<const S*>(a.src);
-    S* __restrict__ dst = static_cast<S*>(a.dst);
     T h[Q];
     static_for<0, Q>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
@@ -447,7 +509,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
       const uint32_t sy = cy(k) > 0 ? ym : (cy(k) < 0 ? yp : y);
       const uint32_t sz = cz(k) > 0 ? zm : (cz(k) < 0 ? zp : z);
       const uint32_t idx = (sz * a.ny + sy) * a.nx + sx;
-      h[k] = Storage<S>::load(src + size_t(k) * a.N + idx);
+      h[k] = Storage<S>::load(static_cast<const S*>(a.src_pop[k]) + idx);
     });
     const int fx = px ? 0 : (x == 0 ? 1 : (x == a.nx - 1 ? 2 : 0));
     const int fy = py ? 0 : (y == 0 ? 1 : (y == a.ny - 1 ? 2 : 0));
@@ -459,7 +521,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
     collide(h, m, omega_of<T>(a));
     static_for<0, Q>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
-      dst[size_t(k) * a.N + cell] = Storage<S>::store(h[k]);
+      static_cast<S*>(a.dst_pop[k])[cell] = Storage<S>::store(h[k]);
     });
   }
   if constexpr (RESID) block_sum4(red, a.partials + 4ull * blk);
@@ -468,12 +530,12 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
 // Resident 256-thread blocks per SM each sweep variant is compiled for (the register
 // budget is 65536 / (256 * blocks)). The float sweeps are memory-bound and need many
 // warps in flight to hide DRAM latency: 6 blocks (<= 42 registers) for the plain
-// single-lattice step; the residual and batched variants carry more state and get one
-// or two blocks fewer so that they do not spill. The FP64 sweeps are bound by the
+// single-lattice step; the residual variant (5) and the batched variants (4) carry
+// more state and get fewer blocks so that they do not spill. The FP64 sweeps are bound by the
 // FP64 pipe and get room for their double registers.
 template <typename S, bool RESID, bool BATCHED>
 struct SweepOccupancy {
-  static constexpr int blocks = 6 - (RESID ? 1 : 0) - (BATCHED ? 1 : 0);
+  static constexpr int blocks = BATCHED ? 4 : (RESID ? 5 : 6);
 };
 template <bool RESID, bool BATCHED>
 struct SweepOccupancy<double, RESID, BATCHED> {
@@ -518,10 +580,16 @@ __global__ void __launch_bounds__(SWEEP_THREADS, (SweepOccupancy<S, RESID, true>
       uint32_t* to = reinterpret_cast<uint32_t*>(&sa);
       for (uint32_t w = threadIdx.x; w < sizeof(SweepArgs) / 4; w += SWEEP_THREADS) to[w] = from[w];
       __syncthreads();
-      if (threadIdx.x == 0) {
+      if (threadIdx.x < Q) {
         const uint32_t c = (e->cur ^ parity) & 1u;
-        sa.src = e->buf[c];
-        sa.dst = const_cast<void*>(e->buf[c ^ 1u]);
+        const S* src = static_cast<const S*>(e->buf[c]);
+        S* dst = static_cast<S*>(const_cast<void*>(e->buf[c ^ 1u]));
+        sa.src_pop[threadIdx.x] = src + size_t(threadIdx.x) * e->a.N;
+        sa.dst_pop[threadIdx.x] = dst + size_t(threadIdx.x) * e->a.N;
+        if (threadIdx.x == 0) {
+          sa.src = src;
+          sa.dst = dst;
+        }
       }
       lat_begin = e->block_begin;
       lat_end = e->block_begin + e->nblocks;

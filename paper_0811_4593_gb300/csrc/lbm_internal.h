@@ -32,9 +32,10 @@ __device__ __forceinline__ uint32_t fdiv(const FastDiv& f, uint32_t n) {
 }
 #endif
 
-// Prescribed velocity of one velocity-face node as the sweep reads it: the velocity in
-// double and float, and 1 / (1 - u.n) for the density relation (n = inward normal),
-// formed in double on the host.
+// One boundary-face node as the sweep reads it. Velocity face: the prescribed velocity
+// in double and float, and 1 / (1 - u.n) for the density relation (n = inward normal),
+// formed in double on the host. Pressure face: the tangential velocity (normal part
+// zero) in double and float, and the prescribed density in `inv`.
 struct __align__(16) FaceNode {
   double u[3];
   double inv;
@@ -52,9 +53,12 @@ struct FaceBC {
 struct SweepArgs {
   const void* src;   // storage [19][N], post-collision state of the previous step
   void* dst;         // storage [19][N], post-collision state after this step
+  const void* src_pop[19];  // src + k N: the start of population k (set with src / dst
+  void* dst_pop[19];        // so that each access is one add and one wide multiply-add)
   uint32_t nx, ny, nz, N;
   FastDiv div_nx, div_ny;
   uint32_t periodic;  // bit a set: axis a is periodic
+  uint32_t pressure;  // bit f set: face f is a pressure face
   double rho0;
   double omega;       // 1 / tau
   float rho0f, omegaf;

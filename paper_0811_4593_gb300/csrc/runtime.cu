@@ -148,16 +148,15 @@ void ctx_free_all(lbm_ctx* ctx) {
   ctx->device_bytes = 0;
 }
 
-// Sweep record of a prescribed velocity u on face f: u in double and float and
-// 1 / (1 - u.n) in double (n the face's inward normal; |u.n| < 1 is validated).
-lbm::FaceNode face_node(int f, const double* u) {
+// Sweep record of one node of face f. Velocity face: u in double and float and
+// 1 / (1 - u.n) in double (n the inward normal; |u.n| < 1 is validated). Pressure
+// face: the tangential part of u and, in the `inv` field, the prescribed density.
+lbm::FaceNode face_node(int f, const double* u, bool pressure, double rho) {
   lbm::FaceNode n{};
+  for (int j = 0; j < 3; ++j) n.u[j] = (pressure && j == f / 2) ? 0.0 : u[j];
+  for (int j = 0; j < 3; ++j) n.uf[j] = float(n.u[j]);
   const double un = (f % 2 == 0 ? 1.0 : -1.0) * u[f / 2];
-  for (int j = 0; j < 3; ++j) {
-    n.u[j] = u[j];
-    n.uf[j] = float(u[j]);
-  }
-  n.inv = 1.0 / (1.0 - un);
+  n.inv = pressure ? rho : 1.0 / (1.0 - un);
   n.pad = 0.0f;
   return n;
 }
@@ -173,33 +172,63 @@ lbm_status validate(int nx, int ny, int nz, double tau, const lbm_face_spec* fac
   if (!(tau > 0.5) || !std::isfinite(tau)) return fail(nullptr, LBM_ERR_ARG, "tau must be finite and > 1/2 (got %g)", tau);
   if (!(rho0 > 0.0) || !std::isfinite(rho0)) return fail(nullptr, LBM_ERR_ARG, "rho0 must be finite and > 0 (got %g)", rho0);
   if (prec < LBM_F64 || prec > LBM_F16_SHIFTED) return fail(nullptr, LBM_ERR_ARG, "unknown precision %d", prec);
+  int pressure_axes = 0;
   for (int a = 0; a < 3; ++a) {
     const int k0 = faces[2 * a].kind, k1 = faces[2 * a + 1].kind;
     for (int k : {k0, k1})
-      if (k != LBM_FACE_PERIODIC && k != LBM_FACE_VELOCITY) return fail(nullptr, LBM_ERR_ARG, "axis %d: unknown face kind %d", a, k);
+      if (k != LBM_FACE_PERIODIC && k != LBM_FACE_VELOCITY && k != LBM_FACE_PRESSURE)
+        return fail(nullptr, LBM_ERR_ARG, "axis %d: unknown face kind %d", a, k);
     if ((k0 == LBM_FACE_PERIODIC) != (k1 == LBM_FACE_PERIODIC))
       return fail(nullptr, LBM_ERR_ARG, "axis %d: periodic faces must come in pairs", a);
+    if (k0 == LBM_FACE_PRESSURE || k1 == LBM_FACE_PRESSURE) ++pressure_axes;
   }
+  if (pressure_axes > 1)
+    return fail(nullptr, LBM_ERR_ARG, "pressure faces may lie on one axis only (an edge borders at most one)");
+  auto finite3 = [](const double* u) { return std::isfinite(u[0]) && std::isfinite(u[1]) && std::isfinite(u[2]); };
   for (int f = 0; f < 6; ++f) {
-    if (faces[f].kind != LBM_FACE_VELOCITY) continue;
+    const int kind = faces[f].kind;
+    if (kind == LBM_FACE_PERIODIC) continue;
     const int a = f / 2;
     const double sg = (f % 2 == 0) ? 1.0 : -1.0;
+    const size_t m = size_t(face_n1(f, nx, ny)) * face_n2(f, ny, nz);
     if (faces[f].u_table) {
-      const size_t m = size_t(face_n1(f, nx, ny)) * face_n2(f, ny, nz);
       for (size_t i = 0; i < m; ++i) {
         const double* u = faces[f].u_table + 3 * i;
-        if (!std::isfinite(u[0]) || !std::isfinite(u[1]) || !std::isfinite(u[2]))
-          return fail(nullptr, LBM_ERR_ARG, "face %d: non-finite velocity at table entry %zu", f, i);
-        if (!(std::fabs(sg * u[a]) < 1.0)) return fail(nullptr, LBM_ERR_ARG, "face %d: |u.n| >= 1 at table entry %zu", f, i);
+        if (!finite3(u)) return fail(nullptr, LBM_ERR_ARG, "face %d: non-finite velocity at table entry %zu", f, i);
+        if (kind == LBM_FACE_VELOCITY && !(std::fabs(sg * u[a]) < 1.0))
+          return fail(nullptr, LBM_ERR_ARG, "face %d: |u.n| >= 1 at table entry %zu", f, i);
       }
     } else {
-      const double* u = faces[f].u;
-      if (!std::isfinite(u[0]) || !std::isfinite(u[1]) || !std::isfinite(u[2]))
-        return fail(nullptr, LBM_ERR_ARG, "face %d: non-finite velocity", f);
-      if (!(std::fabs(u[a]) < 1.0)) return fail(nullptr, LBM_ERR_ARG, "face %d: |u.n| >= 1", f);
+      if (!finite3(faces[f].u)) return fail(nullptr, LBM_ERR_ARG, "face %d: non-finite velocity", f);
+      if (kind == LBM_FACE_VELOCITY && !(std::fabs(faces[f].u[a]) < 1.0))
+        return fail(nullptr, LBM_ERR_ARG, "face %d: |u.n| >= 1", f);
+    }
+    if (kind == LBM_FACE_PRESSURE) {
+      if (faces[f].rho_table) {
+        for (size_t i = 0; i < m; ++i) {
+          const double r = faces[f].rho_table[i];
+          if (!(r > 0.0) || !std::isfinite(r))
+            return fail(nullptr, LBM_ERR_ARG, "face %d: density must be finite and > 0 at table entry %zu", f, i);
+        }
+      } else if (!(faces[f].rho > 0.0) || !std::isfinite(faces[f].rho)) {
+        return fail(nullptr, LBM_ERR_ARG, "face %d: density must be finite and > 0 (got %g)", f, faces[f].rho);
+      }
     }
   }
   return LBM_OK;
+}
+
+// Point the sweep at buf[from] -> buf[from ^ 1], with the per-population starts.
+void set_direction(lbm_ctx* ctx, int from) {
+  const size_t es = storage_bytes(ctx->prec);
+  const char* src = static_cast<const char*>(ctx->buf[from]);
+  char* dst = static_cast<char*>(ctx->buf[from ^ 1]);
+  ctx->args.src = src;
+  ctx->args.dst = dst;
+  for (int k = 0; k < 19; ++k) {
+    ctx->args.src_pop[k] = src + size_t(k) * ctx->N * es;
+    ctx->args.dst_pop[k] = dst + size_t(k) * ctx->N * es;
+  }
 }
 
 cudaError_t dispatch_sweep(lbm_ctx* ctx, bool resid) {
@@ -321,14 +350,22 @@ lbm_status lbm_create(int nx, int ny, int nz, double tau, const lbm_face_spec fa
   a.rho0f = float(rho0);
   a.omegaf = float(1.0 / tau);
   const double zero[3] = {0.0, 0.0, 0.0};
+  a.pressure = 0;
   for (int f = 0; f < 6; ++f) {
-    const bool vel = faces[f].kind == LBM_FACE_VELOCITY;
+    const bool open = faces[f].kind != LBM_FACE_PERIODIC;
+    const bool pres = faces[f].kind == LBM_FACE_PRESSURE;
+    if (pres) a.pressure |= 1u << f;
     a.face[f].tab = nullptr;
-    a.face[f].uni = face_node(f, vel ? faces[f].u : zero);
-    if (vel && faces[f].u_table) {
+    a.face[f].uni = face_node(f, open ? faces[f].u : zero, pres, pres ? faces[f].rho : 0.0);
+    const bool per_node = open && (faces[f].u_table || (pres && faces[f].rho_table));
+    if (per_node) {
       const size_t m = size_t(face_n1(f, nx, ny)) * face_n2(f, ny, nz);
       std::vector<lbm::FaceNode> host(m);
-      for (size_t i = 0; i < m; ++i) host[i] = face_node(f, faces[f].u_table + 3 * i);
+      for (size_t i = 0; i < m; ++i) {
+        const double* u = faces[f].u_table ? faces[f].u_table + 3 * i : faces[f].u;
+        const double r = pres ? (faces[f].rho_table ? faces[f].rho_table[i] : faces[f].rho) : 0.0;
+        host[i] = face_node(f, u, pres, r);
+      }
       const size_t bytes = m * sizeof(lbm::FaceNode);
       void* t = ctx_alloc(ctx, bytes);
       if (!t) return bail(fail(ctx, LBM_ERR_OOM, "allocation of face table %d failed", f));
@@ -370,8 +407,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int n) {
   if (!g.ok) return fail(ctx, LBM_ERR_CUDA, "cannot make device %d current", ctx->device);
   if (lbm_status st0 = settle(ctx); st0 != LBM_OK) return st0;
   for (int i = 0; i < n; ++i) {
-    ctx->args.src = ctx->buf[ctx->cur];
-    ctx->args.dst = ctx->buf[ctx->cur ^ 1];
+    set_direction(ctx, ctx->cur);
     LBM_CUDA(ctx, dispatch_sweep(ctx, false), "sweep launch");
     ctx->cur ^= 1;
     ctx->steps += 1;
@@ -390,8 +426,7 @@ lbm_status lbm_step_residual(lbm_ctx* ctx, int n, double* residual, double* mass
   if (st != LBM_OK) return st;
   st = lbm_step(ctx, n - 1);
   if (st != LBM_OK) return st;
-  ctx->args.src = ctx->buf[ctx->cur];
-  ctx->args.dst = ctx->buf[ctx->cur ^ 1];
+  set_direction(ctx, ctx->cur);
   LBM_CUDA(ctx, dispatch_sweep(ctx, true), "residual sweep launch");
   ctx->cur ^= 1;
   ctx->steps += 1;

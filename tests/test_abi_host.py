@@ -62,7 +62,8 @@ def create(b, nx, ny, nz, tau, specs, prec=1, rho0=1.0):
 
 
 @pytest.mark.parametrize("case", ["small_dim", "tau", "unpaired", "normal_speed", "table_speed", "table_nan",
-                                  "rho0", "precision", "too_large", "kind"])
+                                  "rho0", "precision", "too_large", "kind", "two_pressure_axes",
+                                  "pressure_density", "pressure_table_nan"])
 def test_invalid_specifications_are_rejected(L, case):
     b = L
     kinds = [1, 1, 0, 0, 1, 1]
@@ -93,7 +94,20 @@ def test_invalid_specifications_are_rejected(L, case):
         dims = (1024, 1024, 256)
     elif case == "kind":
         kinds = [3, 3, 0, 0, 1, 1]
+    elif case == "two_pressure_axes":
+        kinds = [2, 1, 0, 0, 2, 1]
+    elif case == "pressure_density":
+        kinds = [2, 1, 0, 0, 1, 1]
+    elif case == "pressure_table_nan":
+        kinds = [1, 2, 0, 0, 1, 1]
     specs, keep = make_specs(b, kinds, us, tables)
+    if case == "two_pressure_axes":
+        specs[0].rho = specs[4].rho = 1.0
+    if case == "pressure_table_nan":
+        t = np.ones((8, 8))
+        t[2, 2] = np.nan
+        keep.append(t)
+        specs[1].rho_table = t.ctypes.data_as(C.POINTER(C.c_double))
     st, out = create(b, *dims, tau, specs, prec, rho0)
     assert st == b.LBM_ERR_ARG, (case, st, b.last_error())
     assert not out.value
