@@ -146,22 +146,26 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------
 
 def timed_steps(lat, steps: int, resid_every: int, events: bool):
-    """Issue `steps` time steps, a fused residual every `resid_every`. Returns per-step
-    CUDA events (on the lattice's stream) and the indices of residual steps."""
+    """Issue `steps` time steps, a fused residual every `resid_every`. Returns CUDA
+    events (on the lattice's stream) around each launch group -- one step, or one pair
+    of steps for an AA lattice -- the group sizes, and the indices of residual groups."""
     import torch
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)] if events else None
+    g = 2 if getattr(lat, "scheme", "ab") == "aa" else 1
+    ngroups = steps // g
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(ngroups + 1)] if events else None
     if evs:
         evs[0].record(lat.stream)
     resid = []
-    for s in range(steps):
-        if resid_every and (s + 1) % resid_every == 0:
-            lat.step_residual(1)
-            resid.append(s)
+    for i in range(ngroups):
+        done = (i + 1) * g
+        if resid_every and done % resid_every == 0:
+            lat.step_residual(g)
+            resid.append(i)
         else:
-            lat.step(1)
+            lat.step(g)
         if evs:
-            evs[s + 1].record(lat.stream)
-    return evs, resid
+            evs[i + 1].record(lat.stream)
+    return evs, resid, g
 
 
 def measure(lat, steps, warmup, resid_every, dist_ctx, clock_gpu=None):
@@ -172,16 +176,18 @@ def measure(lat, steps, warmup, resid_every, dist_ctx, clock_gpu=None):
     dist_ctx.barrier()
     torch.cuda.synchronize()
     l0 = lat.info()["kernel_launches"]
-    evs, resid = timed_steps(lat, steps, resid_every, events=True)
+    evs, resid, g = timed_steps(lat, steps, resid_every, events=True)
     torch.cuda.synchronize()
     dist_ctx.barrier()
     clock = clocks.stop() if clocks else None
     launches = lat.info()["kernel_launches"] - l0
-    total_ms = evs[0].elapsed_time(evs[steps])
-    per = [evs[s].elapsed_time(evs[s + 1]) for s in range(steps)]
-    after_sync = {s + 1 for s in resid}
-    plain = [per[s] for s in range(steps) if s not in resid and s not in after_sync]
-    return total_ms, (sum(plain) / len(plain) if plain else total_ms / steps), launches, clock
+    n = len(evs) - 1
+    total_ms = evs[0].elapsed_time(evs[n])
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(n)]
+    after_sync = {i + 1 for i in resid}
+    plain = [per[i] for i in range(n) if i not in resid and i not in after_sync]
+    step_ms = (sum(plain) / len(plain) if plain else total_ms / n) / g
+    return total_ms, step_ms, launches, clock
 
 
 class Dist:
@@ -250,17 +256,18 @@ def profiled_fp64_per_node(wl_name: str):
     return rec.get("fp64_inst_per_node") if rec.get("source_sha") == sweep_source_hash() else None
 
 
-def run_variant(wl, precision, steps, warmup, resid_every, dist_ctx, clocks=None):
+def run_variant(wl, precision, steps, warmup, resid_every, dist_ctx, clocks=None, scheme="ab"):
     import torch
 
     import paper_0811_4593_gb300 as lbm
-    with lbm.Lattice.from_workload(wl, precision) as lat:
+    with lbm.Lattice.from_workload(wl, precision, scheme=scheme) as lat:
         total_ms, step_ms, launches, _ = measure(lat, steps, warmup, resid_every, dist_ctx)
     hbm, _ = measured_hbm_peak()
     ach = BYTES_PER_UPDATE[precision] * wl.cells / (step_ms * 1e-3) / 1e9
     out = {"mlups": wl.cells * steps / (total_ms * 1e-3) / 1e6, "ms_per_step": total_ms / steps,
            "sweep_ms": step_ms, "achieved_gbs": ach, "frac": ach / hbm, "steps": steps,
-           "bytes_per_update": BYTES_PER_UPDATE[precision]}
+           "bytes_per_update": BYTES_PER_UPDATE[precision], "scheme": scheme,
+           "resident_bytes_per_node": BYTES_PER_UPDATE[precision] // (2 if scheme == "aa" else 1)}
     if precision == "f64":
         # the FP64 sweep is bound by the FP64 pipe, not by HBM
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
@@ -374,6 +381,9 @@ def native(args):
             if p != args.precision:
                 vs[p] = run_variant(wl, p, args.variant_steps, 20, args.resid_every, d, clock)
                 torch.cuda.empty_cache()
+        vs[f"{args.precision}_aa"] = run_variant(wl, args.precision, args.variant_steps, 20, args.resid_every, d,
+                                                 clock, scheme="aa")
+        torch.cuda.empty_cache()
         out["variants"] = vs
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)

@@ -59,6 +59,19 @@ typedef enum {
  *                   even); arithmetic as for LBM_F32. */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16_SHIFTED = 2 } lbm_precision;
 
+/* How the populations are streamed between steps (the method, Sec. "Simulation method",
+ * is the same; only the memory traffic pattern differs, and both give the same bits).
+ *  LBM_SCHEME_AB  two arrays: every step pulls f_i(x - c_i) from one array and writes
+ *                 the other (2 x 19 populations per node resident).
+ *  LBM_SCHEME_AA  one array, steps in pairs: a gather-scatter step that reads the
+ *                 population -i of node x - c_i and writes f*_i back to that slot's
+ *                 place, then an in-place step that reads and writes the node's own
+ *                 slots with i and -i exchanged (19 populations per node resident; the
+ *                 same bytes move per step). An AA lattice is observable (macros,
+ *                 residual, population copies) between step pairs only, and lbm_step /
+ *                 lbm_step_residual take an even n. */
+typedef enum { LBM_SCHEME_AB = 0, LBM_SCHEME_AA = 1 } lbm_scheme;
+
 /* Periodic faces wrap streaming to the opposite face (periodic boundaries of the
  * paper's Sec. "Boundary conditions") and must come in pairs. A velocity face applies
  * the on-site velocity condition; a prescribed velocity of zero is the on-site
@@ -104,9 +117,12 @@ LBM_API lbm_status lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, vo
  * densities on pressure faces, which may lie on one axis only. On edges and corners
  * (nodes on two or three non-periodic faces) the no-slip rules of Sec. "On-site
  * no-slip boundary condition" apply and velocity tables are not read there.
- * Ownership: *out is owned by the library until lbm_destroy. */
+ * Ownership: *out is owned by the library until lbm_destroy. The lattice streams with
+ * LBM_SCHEME_AB; lbm_create_scheme chooses the scheme. */
 LBM_API lbm_status lbm_create(int nx, int ny, int nz, double tau, const lbm_face_spec faces[6],
                       lbm_precision prec, double rho0, lbm_ctx** out);
+LBM_API lbm_status lbm_create_scheme(int nx, int ny, int nz, double tau, const lbm_face_spec faces[6],
+                                     lbm_precision prec, double rho0, lbm_scheme scheme, lbm_ctx** out);
 
 /* Release every device buffer of the context (after synchronising its stream) and the
  * context itself. NULL is accepted. */
@@ -164,6 +180,7 @@ typedef struct {
   int64_t bytes_per_update; /* algorithmic bytes moved per node update: 19 loads + 19
                                stores of the storage type */
   int64_t device_bytes;     /* device memory the context holds */
+  int scheme;               /* lbm_scheme */
 } lbm_info_t;
 LBM_API lbm_status lbm_info(const lbm_ctx* ctx, lbm_info_t* out);
 
@@ -204,7 +221,8 @@ LBM_API lbm_status lbm_batch_destroy(lbm_batch* b);
 LBM_API lbm_status lbm_batch_set_stream(lbm_batch* b, void* cuda_stream);
 
 /* Put `ctx` into `slot` (0 <= slot < capacity, empty). The context must have the
- * batch's precision and device and belong to no other batch. Waits for the context's
+ * batch's precision, device and streaming scheme (all attached contexts share one),
+ * belong to no other batch and, for AA, stand between step pairs. Waits for the context's
  * own stream and allocates its residual buffers. While attached, the context's own
  * calls (lbm_step, lbm_macros, ...) first wait for the batch's stream; lbm_destroy
  * detaches it. */
@@ -213,8 +231,8 @@ LBM_API lbm_status lbm_batch_attach(lbm_batch* b, int slot, lbm_ctx* ctx);
 /* Empty `slot` after the batch's queued work has finished (synchronises). */
 LBM_API lbm_status lbm_batch_detach(lbm_batch* b, int slot);
 
-/* Advance every attached lattice by n >= 1 time steps (as lbm_step), asynchronously on
- * the batch's stream. With residual != 0 the last step also forms each lattice's
+/* Advance every attached lattice by n >= 1 time steps (as lbm_step; n even for AA
+ * lattices), asynchronously on the batch's stream. With residual != 0 the last step also forms each lattice's
  * residual and mass exactly as lbm_step_residual does (same snapshot semantics); read
  * them with lbm_batch_results. */
 LBM_API lbm_status lbm_batch_step(lbm_batch* b, int n, int residual);

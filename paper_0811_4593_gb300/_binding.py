@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "liblbm.so")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_STATE = 0, -1, -2, -3, -4, -5
 PRECISIONS = {"f64": 0, "f32": 1, "f16": 2}
+SCHEMES = {"ab": 0, "aa": 1}
 STORAGE_DTYPE = {"f64": np.float64, "f32": np.float32, "f16": np.float16}
 LBM_HOST, LBM_DEVICE = 0, 1
 FACE_PERIODIC, FACE_VELOCITY, FACE_PRESSURE = 0, 1, 2
@@ -27,6 +28,8 @@ EXPORTS = {
     "lbm_set_allocator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_int, C.c_double,
                              C.POINTER(C.c_void_p)]),
+    "lbm_create_scheme": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_int, C.c_double,
+                                    C.c_int, C.POINTER(C.c_void_p)]),
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_step": (C.c_int, [C.c_void_p, C.c_int]),
@@ -69,7 +72,7 @@ class Pressure:
 class Info(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("precision", C.c_int),
                 ("steps", C.c_int64), ("kernel_launches", C.c_int64), ("bytes_per_update", C.c_int64),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("scheme", C.c_int)]
 
 
 class LBMError(RuntimeError):
@@ -198,11 +201,12 @@ class Lattice:
     (periodic), a velocity 3-vector, a table of prescribed velocities (n2, n1, 3), or a
     Pressure (prescribed density and tangential velocity).
     ``precision`` is "f64" (f stored as double), "f32" or "f16" (f - w rho0 stored as
-    float or binary16).
+    float or binary16). ``scheme`` is "ab" (two arrays) or "aa" (one array, steps in
+    pairs).
     """
 
     def __init__(self, nx, ny, nz, tau, faces, precision="f32", rho0=1.0, stream=None,
-                 torch_allocator=True):
+                 torch_allocator=True, scheme="ab"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the lattice runs only on the GPU")
@@ -211,12 +215,13 @@ class Lattice:
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.tau, self.rho0 = float(tau), float(rho0)
         self.precision = precision
+        self.scheme = scheme
         self.device = torch.cuda.current_device()
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         specs, keep = _face_specs(self.nx, self.ny, self.nz, faces)
         out = C.c_void_p()
-        st = lib().lbm_create(self.nx, self.ny, self.nz, self.tau, C.cast(specs, C.c_void_p),
-                              PRECISIONS[precision], self.rho0, C.byref(out))
+        st = lib().lbm_create_scheme(self.nx, self.ny, self.nz, self.tau, C.cast(specs, C.c_void_p),
+                                     PRECISIONS[precision], self.rho0, SCHEMES[scheme], C.byref(out))
         del keep
         check(st)
         self._ctx = out

@@ -480,8 +480,18 @@ __device__ __forceinline__ void residual_terms(const Moments<T>& m, double rho0,
 // ---------------------------------------------------------------------------------
 // The fused time step: pull stream, classify, close, collide, store.
 // ---------------------------------------------------------------------------------
-// Block `blk` (nodes blk*256 .. blk*256+255) of the lattice described by `a`.
-template <typename S, bool RESID>
+enum StreamMode : int { STREAM_AB = 0, STREAM_AA_GATHER = 1, STREAM_AA_LOCAL = 2 };
+// Block `blk` (nodes blk*256 .. blk*256+255) of the lattice described by `a`, with the
+// streaming scheme MODE:
+//   STREAM_AB         pull f_i(x) = src_i(x - c_i), store dst_i(x)          (two arrays)
+//   STREAM_AA_GATHER  read slot -i of node x - c_i, write f*_i back to slot i of node
+//                     x + c_i -- the location the read of -i came from   (one array)
+//   STREAM_AA_LOCAL   read slot i of node x, write f*_i to slot -i of node x (one array)
+// The two AA steps alternate starting from a state that holds f*_i(x) in slot -i of
+// node x (the "swapped" state); after the gather step the array holds the streamed
+// populations in natural slots, after the local step the swapped post-collision state
+// again. Each node reads and writes the same 19 locations, so one array suffices.
+template <typename S, bool RESID, int MODE>
 __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
   using T = typename ComputeOf<S>::T;
   const uint32_t cell = blk * SWEEP_THREADS + threadIdx.x;
@@ -502,14 +512,25 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
     const uint32_t yp = (y + 1 < a.ny) ? y + 1 : (py ? 0 : a.ny - 1);
     const uint32_t zm = z ? z - 1 : (pz ? a.nz - 1 : 0);
     const uint32_t zp = (z + 1 < a.nz) ? z + 1 : (pz ? 0 : a.nz - 1);
-    T h[Q];
-    static_for<0, Q>([&](auto kc) {
+    // node the population k is pulled from (x - c_k); for STREAM_AA_GATHER also the node
+    // f*_{-k} is pushed to
+    auto pull_idx = [&](auto kc) {
       constexpr int k = decltype(kc)::value;
       const uint32_t sx = cx(k) > 0 ? xm : (cx(k) < 0 ? xp : x);
       const uint32_t sy = cy(k) > 0 ? ym : (cy(k) < 0 ? yp : y);
       const uint32_t sz = cz(k) > 0 ? zm : (cz(k) < 0 ? zp : z);
-      const uint32_t idx = (sz * a.ny + sy) * a.nx + sx;
-      h[k] = Storage<S>::load(static_cast<const S*>(a.src_pop[k]) + idx);
+      return (sz * a.ny + sy) * a.nx + sx;
+    };
+    T h[Q];
+    static_for<0, Q>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      if constexpr (MODE == STREAM_AB) {
+        h[k] = Storage<S>::load(static_cast<const S*>(a.src_pop[k]) + pull_idx(kc));
+      } else if constexpr (MODE == STREAM_AA_GATHER) {
+        h[k] = Storage<S>::load(static_cast<const S*>(a.src_pop[opp(k)]) + pull_idx(kc));
+      } else {
+        h[k] = Storage<S>::load(static_cast<const S*>(a.src_pop[k]) + cell);
+      }
     });
     const int fx = px ? 0 : (x == 0 ? 1 : (x == a.nx - 1 ? 2 : 0));
     const int fy = py ? 0 : (y == 0 ? 1 : (y == a.ny - 1 ? 2 : 0));
@@ -521,7 +542,19 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
     collide(h, m, omega_of<T>(a));
     static_for<0, Q>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
-      static_cast<S*>(a.dst_pop[k])[cell] = Storage<S>::store(h[k]);
+      if constexpr (MODE == STREAM_AB) {
+        static_cast<S*>(a.dst_pop[k])[cell] = Storage<S>::store(h[k]);
+      } else if constexpr (MODE == STREAM_AA_LOCAL) {
+        static_cast<S*>(a.dst_pop[opp(k)])[cell] = Storage<S>::store(h[k]);
+      } else {
+        // push f*_k to node x + c_k = the pull source of -k; a target outside a walled
+        // axis does not exist (the population leaves the domain)
+        constexpr int o = opp(k);
+        const bool inside = code == 0 || !((fx == 1 && cx(o) > 0) || (fx == 2 && cx(o) < 0) ||
+                                           (fy == 1 && cy(o) > 0) || (fy == 2 && cy(o) < 0) ||
+                                           (fz == 1 && cz(o) > 0) || (fz == 2 && cz(o) < 0));
+        if (inside) static_cast<S*>(a.dst_pop[k])[pull_idx(std::integral_constant<int, o>{})] = Storage<S>::store(h[k]);
+      }
     });
   }
   if constexpr (RESID) block_sum4(red, a.partials + 4ull * blk);
@@ -533,27 +566,32 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
 // single-lattice step; the residual variant (5) and the batched variants (4) carry
 // more state and get fewer blocks so that they do not spill. The FP64 sweeps are bound by the
 // FP64 pipe and get room for their double registers.
-template <typename S, bool RESID, bool BATCHED>
+// The AA gather-scatter step also keeps its push targets and takes 2 blocks fewer, the
+// AA in-place step one fewer.
+template <typename S, bool RESID, bool BATCHED, int MODE>
 struct SweepOccupancy {
-  static constexpr int blocks = BATCHED ? 4 : (RESID ? 5 : 6);
+  static constexpr int base = BATCHED ? 4 : (RESID ? 5 : 6);
+  static constexpr int blocks = MODE == 1 ? (base > 4 ? 4 : base - 1) : (MODE == 2 ? (base > 5 ? 5 : base) : base);
 };
-template <bool RESID, bool BATCHED>
-struct SweepOccupancy<double, RESID, BATCHED> {
-  static constexpr int blocks = (RESID && BATCHED) ? 2 : 3;
+template <bool RESID, bool BATCHED, int MODE>
+struct SweepOccupancy<double, RESID, BATCHED, MODE> {
+  static constexpr int blocks = (RESID && BATCHED) || MODE == 1 ? 2 : 3;
 };
 
-template <typename S, bool RESID>
-__global__ void __launch_bounds__(SWEEP_THREADS, (SweepOccupancy<S, RESID, false>::blocks))
+template <typename S, bool RESID, int MODE>
+__global__ void __launch_bounds__(SWEEP_THREADS, (SweepOccupancy<S, RESID, false, MODE>::blocks))
     sweep_kernel(const __grid_constant__ SweepArgs a) {
-  sweep_block<S, RESID>(a, blockIdx.x);
+  sweep_block<S, RESID, MODE>(a, blockIdx.x);
 }
 
 // One time step of every lattice of a batch. A persistent grid splits the batch's
 // global block range into one contiguous share per CTA; a CTA caches the descriptor of
 // the lattice it is in (in shared memory) and runs the same per-block code as the
 // single-lattice sweep, so every lattice computes the same bits alone or in a batch.
-template <typename S, bool RESID>
-__global__ void __launch_bounds__(SWEEP_THREADS, (SweepOccupancy<S, RESID, true>::blocks))
+// AB lattices: `parity` picks the direction buf[cur ^ parity] -> buf[cur ^ parity ^ 1].
+// AA lattices (MODE != STREAM_AB): both slots of buf[] are the one array.
+template <typename S, bool RESID, int MODE>
+__global__ void __launch_bounds__(SWEEP_THREADS, (SweepOccupancy<S, RESID, true, MODE>::blocks))
     sweep_batched_kernel(const BatchHeader* __restrict__ hdr, const BatchEntry* __restrict__ ents, uint32_t parity) {
   __shared__ SweepArgs sa;
   __shared__ uint32_t s_idx;
@@ -595,14 +633,15 @@ __global__ void __launch_bounds__(SWEEP_THREADS, (SweepOccupancy<S, RESID, true>
       lat_end = e->block_begin + e->nblocks;
       __syncthreads();
     }
-    sweep_block<S, RESID>(sa, b - lat_begin);
+    sweep_block<S, RESID, MODE>(sa, b - lat_begin);
     if constexpr (RESID) __syncthreads();  // the block-sum buffer is reused by the next block
     ++b;
   }
 }
 
 // Stored state -> residual terms (no streaming, no update).
-template <typename S>
+// SWAPPED: the state holds f_k in slot -k (an AA lattice after a local step).
+template <typename S, bool SWAPPED = false>
 __global__ void __launch_bounds__(SWEEP_THREADS)
     state_reduce_kernel(const S* __restrict__ src, uint32_t N, double rho0, void* snap, double* partials) {
   using T = typename ComputeOf<S>::T;
@@ -612,7 +651,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS)
     T h[Q];
     static_for<0, Q>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
-      h[k] = Storage<S>::load(src + size_t(k) * N + cell);
+      h[k] = Storage<S>::load(src + size_t(SWAPPED ? opp(k) : k) * N + cell);
     });
     const double ref = ref_rho<S>(rho0);
     const Moments<T> m = moments(h, T(ref));
@@ -634,7 +673,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS) init_kernel(S* __restrict__ dst
   });
 }
 
-template <typename S>
+template <typename S, bool SWAPPED>
 __global__ void __launch_bounds__(SWEEP_THREADS)
     macros_kernel(const S* __restrict__ src, uint32_t N, double rho0, typename ComputeOf<S>::T* rho,
                   typename ComputeOf<S>::T* u) {
@@ -644,7 +683,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS)
   T h[Q];
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    h[k] = Storage<S>::load(src + size_t(k) * N + cell);
+    h[k] = Storage<S>::load(src + size_t(SWAPPED ? opp(k) : k) * N + cell);
   });
   const Moments<T> m = moments(h, T(ref_rho<S>(rho0)));
   if (rho) rho[cell] = m.rho;
@@ -658,11 +697,18 @@ __global__ void __launch_bounds__(SWEEP_THREADS)
 // ---------------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------------
-template <typename S>
-cudaError_t launch_sweep_impl(const SweepArgs& a, bool resid, cudaStream_t s) {
+template <typename S, int MODE>
+void launch_sweep_mode(const SweepArgs& a, bool resid, cudaStream_t s) {
   const uint32_t blocks = sweep_blocks(a.N);
-  if (resid) sweep_kernel<S, true><<<blocks, SWEEP_THREADS, 0, s>>>(a);
-  else sweep_kernel<S, false><<<blocks, SWEEP_THREADS, 0, s>>>(a);
+  if (resid) sweep_kernel<S, true, MODE><<<blocks, SWEEP_THREADS, 0, s>>>(a);
+  else sweep_kernel<S, false, MODE><<<blocks, SWEEP_THREADS, 0, s>>>(a);
+}
+
+template <typename S>
+cudaError_t launch_sweep_impl(const SweepArgs& a, bool resid, int mode, cudaStream_t s) {
+  if (mode == STREAM_AA_GATHER) launch_sweep_mode<S, STREAM_AA_GATHER>(a, resid, s);
+  else if (mode == STREAM_AA_LOCAL) launch_sweep_mode<S, STREAM_AA_LOCAL>(a, resid, s);
+  else launch_sweep_mode<S, STREAM_AB>(a, resid, s);
   return cudaGetLastError();
 }
 
@@ -673,26 +719,43 @@ cudaError_t launch_init_impl(void* dst, uint32_t N, double rho0, cudaStream_t s)
 }
 
 template <typename S>
-cudaError_t launch_macros_impl(const void* src, uint32_t N, double rho0, void* rho, void* u, cudaStream_t s) {
+cudaError_t launch_macros_impl(const void* src, uint32_t N, double rho0, void* rho, void* u, bool swapped,
+                               cudaStream_t s) {
   using T = typename ComputeOf<S>::T;
-  macros_kernel<S><<<sweep_blocks(N), SWEEP_THREADS, 0, s>>>(static_cast<const S*>(src), N, rho0,
-                                                             static_cast<T*>(rho), static_cast<T*>(u));
+  if (swapped)
+    macros_kernel<S, true><<<sweep_blocks(N), SWEEP_THREADS, 0, s>>>(static_cast<const S*>(src), N, rho0,
+                                                                     static_cast<T*>(rho), static_cast<T*>(u));
+  else
+    macros_kernel<S, false><<<sweep_blocks(N), SWEEP_THREADS, 0, s>>>(static_cast<const S*>(src), N, rho0,
+                                                                      static_cast<T*>(rho), static_cast<T*>(u));
   return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t launch_state_reduce_impl(const void* src, uint32_t N, double rho0, void* snap, double* partials,
-                                     cudaStream_t s) {
-  state_reduce_kernel<S><<<sweep_blocks(N), SWEEP_THREADS, 0, s>>>(static_cast<const S*>(src), N, rho0, snap,
-                                                                   partials);
+                                     bool swapped, cudaStream_t s) {
+  if (swapped)
+    state_reduce_kernel<S, true><<<sweep_blocks(N), SWEEP_THREADS, 0, s>>>(static_cast<const S*>(src), N, rho0,
+                                                                           snap, partials);
+  else
+    state_reduce_kernel<S, false><<<sweep_blocks(N), SWEEP_THREADS, 0, s>>>(static_cast<const S*>(src), N, rho0,
+                                                                            snap, partials);
   return cudaGetLastError();
+}
+
+template <typename S, int MODE>
+void launch_batched_mode(const BatchHeader* hdr, const BatchEntry* ents, uint32_t parity, bool resid, int grid,
+                         cudaStream_t s) {
+  if (resid) sweep_batched_kernel<S, true, MODE><<<grid, SWEEP_THREADS, 0, s>>>(hdr, ents, parity);
+  else sweep_batched_kernel<S, false, MODE><<<grid, SWEEP_THREADS, 0, s>>>(hdr, ents, parity);
 }
 
 template <typename S>
 cudaError_t launch_sweep_batched_impl(const BatchHeader* hdr, const BatchEntry* ents, uint32_t parity, bool resid,
-                                      int grid, cudaStream_t s) {
-  if (resid) sweep_batched_kernel<S, true><<<grid, SWEEP_THREADS, 0, s>>>(hdr, ents, parity);
-  else sweep_batched_kernel<S, false><<<grid, SWEEP_THREADS, 0, s>>>(hdr, ents, parity);
+                                      int mode, int grid, cudaStream_t s) {
+  if (mode == STREAM_AA_GATHER) launch_batched_mode<S, STREAM_AA_GATHER>(hdr, ents, parity, resid, grid, s);
+  else if (mode == STREAM_AA_LOCAL) launch_batched_mode<S, STREAM_AA_LOCAL>(hdr, ents, parity, resid, grid, s);
+  else launch_batched_mode<S, STREAM_AB>(hdr, ents, parity, resid, grid, s);
   return cudaGetLastError();
 }
 
@@ -701,31 +764,42 @@ int batched_grid_impl() {
   int dev = 0, sms = 0, a = 0, b = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sweep_batched_kernel<S, false>, SWEEP_THREADS, 0) != cudaSuccess)
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_batched_kernel<S, true>, SWEEP_THREADS, 0) != cudaSuccess)
-    return 0;
-  return sms * (a < b ? a : b);
+  // the smallest residency over the variants the batch launches
+  int best = 1 << 30;
+  auto take = [&](const void* fn) {
+    int r = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, fn, SWEEP_THREADS, 0) != cudaSuccess) r = 0;
+    best = r < best ? r : best;
+  };
+  take(reinterpret_cast<const void*>(sweep_batched_kernel<S, false, STREAM_AB>));
+  take(reinterpret_cast<const void*>(sweep_batched_kernel<S, true, STREAM_AB>));
+  take(reinterpret_cast<const void*>(sweep_batched_kernel<S, false, STREAM_AA_GATHER>));
+  take(reinterpret_cast<const void*>(sweep_batched_kernel<S, false, STREAM_AA_LOCAL>));
+  take(reinterpret_cast<const void*>(sweep_batched_kernel<S, true, STREAM_AA_LOCAL>));
+  (void)a;
+  (void)b;
+  return sms * best;
 }
 
 #define LBM_INSTANTIATE(S)                                                                              \
-  template <> cudaError_t launch_sweep<S>(const SweepArgs& a, bool resid, cudaStream_t s) {             \
-    return launch_sweep_impl<S>(a, resid, s);                                                           \
+  template <> cudaError_t launch_sweep<S>(const SweepArgs& a, bool resid, int mode, cudaStream_t s) {   \
+    return launch_sweep_impl<S>(a, resid, mode, s);                                                     \
   }                                                                                                     \
   template <> cudaError_t launch_init<S>(void* dst, uint32_t N, double rho0, cudaStream_t s) {          \
     return launch_init_impl<S>(dst, N, rho0, s);                                                        \
   }                                                                                                     \
   template <> cudaError_t launch_macros<S>(const void* src, uint32_t N, double rho0, void* rho, void* u, \
-                                           cudaStream_t s) {                                            \
-    return launch_macros_impl<S>(src, N, rho0, rho, u, s);                                              \
+                                           bool swapped, cudaStream_t s) {                              \
+    return launch_macros_impl<S>(src, N, rho0, rho, u, swapped, s);                                     \
   }                                                                                                     \
   template <> cudaError_t launch_state_reduce<S>(const void* src, uint32_t N, double rho0, void* snap,  \
-                                                 double* partials, cudaStream_t s) {                   \
-    return launch_state_reduce_impl<S>(src, N, rho0, snap, partials, s);                                \
+                                                 double* partials, bool swapped, cudaStream_t s) {     \
+    return launch_state_reduce_impl<S>(src, N, rho0, snap, partials, swapped, s);                       \
   }                                                                                                     \
   template <> cudaError_t launch_sweep_batched<S>(const BatchHeader* hdr, const BatchEntry* ents,       \
-                                                  uint32_t parity, bool resid, int grid, cudaStream_t s) { \
-    return launch_sweep_batched_impl<S>(hdr, ents, parity, resid, grid, s);                            \
+                                                  uint32_t parity, bool resid, int mode, int grid,      \
+                                                  cudaStream_t s) {                                     \
+    return launch_sweep_batched_impl<S>(hdr, ents, parity, resid, mode, grid, s);                      \
   }                                                                                                     \
   template <> int batched_grid<S>() { return batched_grid_impl<S>(); }
 

@@ -88,15 +88,17 @@ constexpr int REDUCE_THREADS = 1024;
 
 inline uint32_t sweep_blocks(uint32_t N) { return (N + SWEEP_THREADS - 1) / SWEEP_THREADS; }
 
-template <typename S> cudaError_t launch_sweep(const SweepArgs& a, bool resid, cudaStream_t s);
+// mode: 0 A/B pull, 1 AA gather-scatter step, 2 AA in-place step (see kernels.cuh)
+template <typename S> cudaError_t launch_sweep(const SweepArgs& a, bool resid, int mode, cudaStream_t s);
 template <typename S> cudaError_t launch_init(void* dst, uint32_t N, double rho0, cudaStream_t s);
+// swapped: the state holds f_k in slot -k (an AA lattice between step pairs)
 template <typename S> cudaError_t launch_macros(const void* src, uint32_t N, double rho0, void* rho,
-                                                void* u, cudaStream_t s);
+                                                void* u, bool swapped, cudaStream_t s);
 template <typename S> cudaError_t launch_state_reduce(const void* src, uint32_t N, double rho0,
-                                                      void* snap, double* partials, cudaStream_t s);
+                                                      void* snap, double* partials, bool swapped, cudaStream_t s);
 cudaError_t launch_final_reduce(const double* partials, uint32_t nblocks, double* out, cudaStream_t s);
 template <typename S> cudaError_t launch_sweep_batched(const BatchHeader* hdr, const BatchEntry* ents, uint32_t parity,
-                                                       bool resid, int grid, cudaStream_t s);
+                                                       bool resid, int mode, int grid, cudaStream_t s);
 template <typename S> int batched_grid();  // persistent grid size: SMs x resident blocks per SM
 cudaError_t launch_batch_final_reduce(const BatchHeader* hdr, const BatchEntry* ents, int capacity, double* results,
                                       cudaStream_t s);

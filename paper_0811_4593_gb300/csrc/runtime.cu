@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/lbm.h"
+#include "d3q19.cuh"
 #include "lbm_internal.h"
 
 namespace {
@@ -34,9 +35,10 @@ struct lbm_ctx {
   uint32_t N = 0;
   double tau = 1.0, rho0 = 1.0;
   lbm_precision prec = LBM_F32;
+  lbm_scheme scheme = LBM_SCHEME_AB;
   lbm::SweepArgs args{};
-  void* buf[2] = {nullptr, nullptr};
-  int cur = 0;  // buf[cur] holds the current post-collision state
+  void* buf[2] = {nullptr, nullptr};  // AA: both entries are the one population array
+  int cur = 0;  // A/B: buf[cur] holds the current post-collision state
   void* snap = nullptr;
   double* partials = nullptr;
   double* dred = nullptr;
@@ -55,6 +57,7 @@ struct lbm_batch {
   int device = 0;
   int capacity = 0;
   lbm_precision prec = LBM_F32;
+  int scheme = -1;  // scheme of the attached contexts (-1: none attached yet)
   std::vector<lbm_ctx*> slots;
   std::vector<uint8_t> has_result;  // slot took part in the last residual step
   lbm::BatchHeader* h_hdr = nullptr;  // pinned host mirror of the device table
@@ -71,6 +74,7 @@ struct lbm_batch {
   struct Graph {
     int n;
     bool resid;
+    int scheme;
     cudaGraphExec_t exec;
   };
   std::vector<Graph> graphs;
@@ -231,12 +235,28 @@ void set_direction(lbm_ctx* ctx, int from) {
   }
 }
 
+// Streaming mode of the context's next step: A/B pull, or for AA the gather-scatter
+// step after an even number of steps and the in-place step after an odd one.
+int next_mode(const lbm_ctx* ctx) {
+  if (ctx->scheme == LBM_SCHEME_AB) return 0;
+  return (ctx->steps % 2 == 0) ? 1 : 2;
+}
+
 cudaError_t dispatch_sweep(lbm_ctx* ctx, bool resid) {
+  const int mode = next_mode(ctx);
   switch (ctx->prec) {
-    case LBM_F64: return lbm::launch_sweep<double>(ctx->args, resid, ctx->stream);
-    case LBM_F32: return lbm::launch_sweep<float>(ctx->args, resid, ctx->stream);
-    default: return lbm::launch_sweep<__half>(ctx->args, resid, ctx->stream);
+    case LBM_F64: return lbm::launch_sweep<double>(ctx->args, resid, mode, ctx->stream);
+    case LBM_F32: return lbm::launch_sweep<float>(ctx->args, resid, mode, ctx->stream);
+    default: return lbm::launch_sweep<__half>(ctx->args, resid, mode, ctx->stream);
   }
+}
+
+// Observations (macros, residual, population copies) need the post-collision state:
+// always for A/B, between step pairs for AA (where population k sits in slot -k).
+lbm_status require_observable(lbm_ctx* ctx) {
+  if (ctx->scheme == LBM_SCHEME_AA && ctx->steps % 2 != 0)
+    return fail(ctx, LBM_ERR_STATE, "an AA lattice is observable only after an even number of steps");
+  return LBM_OK;
 }
 
 cudaError_t dispatch_init(lbm_ctx* ctx, void* dst) {
@@ -305,8 +325,14 @@ lbm_status lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void* user
 
 lbm_status lbm_create(int nx, int ny, int nz, double tau, const lbm_face_spec faces[6], lbm_precision prec,
                       double rho0, lbm_ctx** out) {
+  return lbm_create_scheme(nx, ny, nz, tau, faces, prec, rho0, LBM_SCHEME_AB, out);
+}
+
+lbm_status lbm_create_scheme(int nx, int ny, int nz, double tau, const lbm_face_spec faces[6], lbm_precision prec,
+                             double rho0, lbm_scheme scheme, lbm_ctx** out) {
   if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
   *out = nullptr;
+  if (scheme != LBM_SCHEME_AB && scheme != LBM_SCHEME_AA) return fail(nullptr, LBM_ERR_ARG, "unknown scheme %d", int(scheme));
   lbm_status st = validate(nx, ny, nz, tau, faces, prec, rho0);
   if (st != LBM_OK) return st;
   lbm_ctx* ctx = new (std::nothrow) lbm_ctx();
@@ -321,7 +347,7 @@ lbm_status lbm_create(int nx, int ny, int nz, double tau, const lbm_face_spec fa
   }
   ctx->nx = nx; ctx->ny = ny; ctx->nz = nz;
   ctx->N = uint32_t(nx) * uint32_t(ny) * uint32_t(nz);
-  ctx->tau = tau; ctx->rho0 = rho0; ctx->prec = prec;
+  ctx->tau = tau; ctx->rho0 = rho0; ctx->prec = prec; ctx->scheme = scheme;
 
   auto bail = [&](lbm_status s) {
     g_err = ctx->err;
@@ -331,10 +357,11 @@ lbm_status lbm_create(int nx, int ny, int nz, double tau, const lbm_face_spec fa
     return s;
   };
   const size_t pop_bytes = 19ull * ctx->N * storage_bytes(prec);
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < (scheme == LBM_SCHEME_AA ? 1 : 2); ++b) {
     ctx->buf[b] = ctx_alloc(ctx, pop_bytes);
     if (!ctx->buf[b]) return bail(fail(ctx, LBM_ERR_OOM, "allocation of %zu bytes for populations failed", pop_bytes));
   }
+  if (scheme == LBM_SCHEME_AA) ctx->buf[1] = ctx->buf[0];
   ctx->dred = static_cast<double*>(ctx_alloc(ctx, 4 * sizeof(double)));
   if (!ctx->dred) return bail(fail(ctx, LBM_ERR_OOM, "allocation of the reduction result failed"));
 
@@ -403,13 +430,15 @@ lbm_status lbm_set_stream(lbm_ctx* ctx, void* cuda_stream) {
 lbm_status lbm_step(lbm_ctx* ctx, int n) {
   if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
   if (n < 0) return fail(ctx, LBM_ERR_ARG, "n must be >= 0 (got %d)", n);
+  if (ctx->scheme == LBM_SCHEME_AA && n % 2 != 0)
+    return fail(ctx, LBM_ERR_ARG, "an AA lattice advances in pairs of steps (got n = %d)", n);
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, LBM_ERR_CUDA, "cannot make device %d current", ctx->device);
   if (lbm_status st0 = settle(ctx); st0 != LBM_OK) return st0;
   for (int i = 0; i < n; ++i) {
     set_direction(ctx, ctx->cur);
     LBM_CUDA(ctx, dispatch_sweep(ctx, false), "sweep launch");
-    ctx->cur ^= 1;
+    if (ctx->scheme == LBM_SCHEME_AB) ctx->cur ^= 1;
     ctx->steps += 1;
     ctx->launches += 1;
   }
@@ -419,16 +448,25 @@ lbm_status lbm_step(lbm_ctx* ctx, int n) {
 lbm_status lbm_step_residual(lbm_ctx* ctx, int n, double* residual, double* mass) {
   if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
   if (n < 1) return fail(ctx, LBM_ERR_ARG, "n must be >= 1 (got %d)", n);
+  if (ctx->scheme == LBM_SCHEME_AA && n % 2 != 0)
+    return fail(ctx, LBM_ERR_ARG, "an AA lattice advances in pairs of steps (got n = %d)", n);
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, LBM_ERR_CUDA, "cannot make device %d current", ctx->device);
   if (lbm_status st0 = settle(ctx); st0 != LBM_OK) return st0;
+  if (lbm_status st0 = require_observable(ctx); st0 != LBM_OK) return st0;
   lbm_status st = ensure_reduction_buffers(ctx);
   if (st != LBM_OK) return st;
-  st = lbm_step(ctx, n - 1);
-  if (st != LBM_OK) return st;
+  // the n - 1 plain steps (an odd count for AA: issue them one by one)
+  for (int i = 0; i < n - 1; ++i) {
+    set_direction(ctx, ctx->cur);
+    LBM_CUDA(ctx, dispatch_sweep(ctx, false), "sweep launch");
+    if (ctx->scheme == LBM_SCHEME_AB) ctx->cur ^= 1;
+    ctx->steps += 1;
+    ctx->launches += 1;
+  }
   set_direction(ctx, ctx->cur);
   LBM_CUDA(ctx, dispatch_sweep(ctx, true), "residual sweep launch");
-  ctx->cur ^= 1;
+  if (ctx->scheme == LBM_SCHEME_AB) ctx->cur ^= 1;
   ctx->steps += 1;
   ctx->launches += 1;
   return finish_reduction(ctx, residual, mass);
@@ -439,13 +477,15 @@ lbm_status lbm_residual(lbm_ctx* ctx, double* residual, double* mass) {
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, LBM_ERR_CUDA, "cannot make device %d current", ctx->device);
   if (lbm_status st0 = settle(ctx); st0 != LBM_OK) return st0;
+  if (lbm_status st0 = require_observable(ctx); st0 != LBM_OK) return st0;
   lbm_status st = ensure_reduction_buffers(ctx);
   if (st != LBM_OK) return st;
+  const bool sw = ctx->scheme == LBM_SCHEME_AA;
   cudaError_t e;
   switch (ctx->prec) {
-    case LBM_F64: e = lbm::launch_state_reduce<double>(ctx->buf[ctx->cur], ctx->N, ctx->rho0, ctx->snap, ctx->partials, ctx->stream); break;
-    case LBM_F32: e = lbm::launch_state_reduce<float>(ctx->buf[ctx->cur], ctx->N, ctx->rho0, ctx->snap, ctx->partials, ctx->stream); break;
-    default: e = lbm::launch_state_reduce<__half>(ctx->buf[ctx->cur], ctx->N, ctx->rho0, ctx->snap, ctx->partials, ctx->stream); break;
+    case LBM_F64: e = lbm::launch_state_reduce<double>(ctx->buf[ctx->cur], ctx->N, ctx->rho0, ctx->snap, ctx->partials, sw, ctx->stream); break;
+    case LBM_F32: e = lbm::launch_state_reduce<float>(ctx->buf[ctx->cur], ctx->N, ctx->rho0, ctx->snap, ctx->partials, sw, ctx->stream); break;
+    default: e = lbm::launch_state_reduce<__half>(ctx->buf[ctx->cur], ctx->N, ctx->rho0, ctx->snap, ctx->partials, sw, ctx->stream); break;
   }
   LBM_CUDA(ctx, e, "state reduction launch");
   ctx->launches += 1;
@@ -458,11 +498,13 @@ lbm_status lbm_macros(lbm_ctx* ctx, void* rho, void* u) {
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, LBM_ERR_CUDA, "cannot make device %d current", ctx->device);
   if (lbm_status st0 = settle(ctx); st0 != LBM_OK) return st0;
+  if (lbm_status st0 = require_observable(ctx); st0 != LBM_OK) return st0;
+  const bool sw = ctx->scheme == LBM_SCHEME_AA;
   cudaError_t e;
   switch (ctx->prec) {
-    case LBM_F64: e = lbm::launch_macros<double>(ctx->buf[ctx->cur], ctx->N, ctx->rho0, rho, u, ctx->stream); break;
-    case LBM_F32: e = lbm::launch_macros<float>(ctx->buf[ctx->cur], ctx->N, ctx->rho0, rho, u, ctx->stream); break;
-    default: e = lbm::launch_macros<__half>(ctx->buf[ctx->cur], ctx->N, ctx->rho0, rho, u, ctx->stream); break;
+    case LBM_F64: e = lbm::launch_macros<double>(ctx->buf[ctx->cur], ctx->N, ctx->rho0, rho, u, sw, ctx->stream); break;
+    case LBM_F32: e = lbm::launch_macros<float>(ctx->buf[ctx->cur], ctx->N, ctx->rho0, rho, u, sw, ctx->stream); break;
+    default: e = lbm::launch_macros<__half>(ctx->buf[ctx->cur], ctx->N, ctx->rho0, rho, u, sw, ctx->stream); break;
   }
   LBM_CUDA(ctx, e, "macros launch");
   ctx->launches += 1;
@@ -477,6 +519,7 @@ static lbm_status copy_populations(lbm_ctx* ctx, void* host_or_dev, int z0, int 
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, LBM_ERR_CUDA, "cannot make device %d current", ctx->device);
   if (lbm_status st0 = settle(ctx); st0 != LBM_OK) return st0;
+  if (lbm_status st0 = require_observable(ctx); st0 != LBM_OK) return st0;
   const size_t es = storage_bytes(ctx->prec);
   const size_t plane = size_t(ctx->nx) * ctx->ny;
   const size_t slab = plane * nzs * es;
@@ -485,7 +528,9 @@ static lbm_status copy_populations(lbm_ctx* ctx, void* host_or_dev, int z0, int 
   cudaMemcpyKind kind = to_ctx ? (where == LBM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice)
                                : (where == LBM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
   for (int k = 0; k < 19; ++k) {
-    char* l = lat + (size_t(k) * ctx->N + size_t(z0) * plane) * es;
+    // an AA lattice keeps population k in slot -k between step pairs
+    const int slot = ctx->scheme == LBM_SCHEME_AA ? lbm::opp(k) : k;
+    char* l = lat + (size_t(slot) * ctx->N + size_t(z0) * plane) * es;
     char* u = user + size_t(k) * slab;
     LBM_CUDA(ctx, cudaMemcpyAsync(to_ctx ? l : u, to_ctx ? u : l, slab, kind, ctx->stream), "population copy");
   }
@@ -519,6 +564,7 @@ lbm_status lbm_info(const lbm_ctx* ctx, lbm_info_t* out) {
   out->kernel_launches = ctx->launches;
   out->bytes_per_update = int64_t(38 * storage_bytes(ctx->prec));
   out->device_bytes = ctx->device_bytes;
+  out->scheme = ctx->scheme;
   return LBM_OK;
 }
 
@@ -582,11 +628,15 @@ static void batch_release(lbm_batch* b) {
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
+// Step i of a batched n-step loop: A/B lattices alternate the buffer direction with
+// the parity; AA lattices (all at a step-pair boundary when a loop starts) alternate
+// the gather-scatter and in-place steps.
 static cudaError_t batch_launch_sweep(lbm_batch* b, uint32_t parity, bool resid) {
+  const int mode = b->scheme == LBM_SCHEME_AA ? (parity ? 2 : 1) : 0;
   switch (b->prec) {
-    case LBM_F64: return lbm::launch_sweep_batched<double>(b->d_hdr, b->d_ent, parity, resid, b->grid, b->stream);
-    case LBM_F32: return lbm::launch_sweep_batched<float>(b->d_hdr, b->d_ent, parity, resid, b->grid, b->stream);
-    default: return lbm::launch_sweep_batched<__half>(b->d_hdr, b->d_ent, parity, resid, b->grid, b->stream);
+    case LBM_F64: return lbm::launch_sweep_batched<double>(b->d_hdr, b->d_ent, parity, resid, mode, b->grid, b->stream);
+    case LBM_F32: return lbm::launch_sweep_batched<float>(b->d_hdr, b->d_ent, parity, resid, mode, b->grid, b->stream);
+    default: return lbm::launch_sweep_batched<__half>(b->d_hdr, b->d_ent, parity, resid, mode, b->grid, b->stream);
   }
 }
 
@@ -678,12 +728,19 @@ lbm_status lbm_batch_attach(lbm_batch* b, int slot, lbm_ctx* ctx) {
   if (ctx->batch) return bfail(b, LBM_ERR_STATE, "context is attached to a batch already");
   if (ctx->prec != b->prec) return bfail(b, LBM_ERR_ARG, "context precision differs from the batch's");
   if (ctx->device != b->device) return bfail(b, LBM_ERR_ARG, "context lives on another device");
+  int attached = 0;
+  for (lbm_ctx* c : b->slots) attached += c ? 1 : 0;
+  if (attached > 0 && int(ctx->scheme) != b->scheme)
+    return bfail(b, LBM_ERR_ARG, "context streaming scheme differs from the batch's");
+  if (ctx->scheme == LBM_SCHEME_AA && ctx->steps % 2 != 0)
+    return bfail(b, LBM_ERR_STATE, "an AA context joins a batch between step pairs only");
   DeviceGuard g(b->device);
   lbm_status st = ensure_reduction_buffers(ctx);
   if (st != LBM_OK) return bfail(b, st, ctx->err.c_str());
   LBM_BCUDA(b, cudaStreamSynchronize(ctx->stream), "waiting for the context's own work");
   b->slots[slot] = ctx;
   b->has_result[slot] = 0;
+  b->scheme = int(ctx->scheme);
   ctx->batch = b;
   ctx->batch_slot = slot;
   return LBM_OK;
@@ -706,6 +763,7 @@ lbm_status lbm_batch_detach(lbm_batch* b, int slot) {
 lbm_status lbm_batch_step(lbm_batch* b, int n, int residual) {
   if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
   if (n < 1) return bfail(b, LBM_ERR_ARG, "n must be >= 1");
+  if (b->scheme == LBM_SCHEME_AA && n % 2 != 0) return bfail(b, LBM_ERR_ARG, "a batch of AA lattices steps in pairs");
   DeviceGuard g(b->device);
   // the previous upload must have read the host mirror before it is rewritten
   LBM_BCUDA(b, cudaEventSynchronize(b->table_free), "waiting for the previous table upload");
@@ -738,7 +796,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n, int residual) {
     // so one graph per (n, residual) serves every membership of the batch
     cudaGraphExec_t exec = nullptr;
     for (auto& gr : b->graphs)
-      if (gr.n == n && gr.resid == resid) exec = gr.exec;
+      if (gr.n == n && gr.resid == resid && gr.scheme == b->scheme) exec = gr.exec;
     if (!exec) {
       cudaGraph_t graph = nullptr;
       LBM_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "beginning graph capture");
@@ -753,7 +811,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n, int residual) {
         cudaGraphExecDestroy(b->graphs.front().exec);
         b->graphs.erase(b->graphs.begin());
       }
-      b->graphs.push_back({n, resid, exec});
+      b->graphs.push_back({n, resid, b->scheme, exec});
     }
     LBM_BCUDA(b, cudaGraphLaunch(exec, b->stream), "launching the step graph");
   } else {
@@ -767,7 +825,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n, int residual) {
     lbm_ctx* c = b->slots[slot];
     b->has_result[slot] = (c && resid) ? 1 : 0;
     if (!c) continue;
-    c->cur ^= (n & 1);
+    if (c->scheme == LBM_SCHEME_AB) c->cur ^= (n & 1);
     c->steps += n;
   }
   b->steps += n;

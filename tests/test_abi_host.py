@@ -115,6 +115,14 @@ def test_invalid_specifications_are_rejected(L, case):
     del keep
 
 
+def test_unknown_scheme_is_rejected(L):
+    b = L
+    specs, keep = make_specs(b, [1, 1, 0, 0, 1, 1])
+    out = C.c_void_p()
+    st = b.lib().lbm_create_scheme(8, 8, 8, 0.8, C.cast(specs, C.c_void_p), 1, 1.0, 5, C.byref(out))
+    assert st == b.LBM_ERR_ARG and not out.value
+
+
 def test_null_arguments(L):
     b = L
     assert b.lib().lbm_step(None, 1) == b.LBM_ERR_ARG
