@@ -402,7 +402,7 @@ def serving(args):
     lib_build.build()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     kw = dict(capacity=args.slots, budget_bytes=args.budget_gb * 1e9, round_steps=args.resid_every,
-              max_steps=args.max_steps, target=args.target, plateau_checks=10)
+              max_steps=args.max_steps, target=args.target, plateau_checks=10, scheme=args.scheme)
     cap_reqs = inp.serving_requests(args.capacity_requests, 1, 1.0)
     cap_jobs = [Job(r.rid, 0.0, inp.request_workload(r)) for r in cap_reqs]
     _, cap = Server(args.precision, **kw).serve(cap_jobs, closed_loop=True)
@@ -424,7 +424,74 @@ def serving(args):
                        "capacity_run": {"jobs": cap["jobs"], "wall_s": round(cap["wall_s"], 2),
                                         "aggregate_mlups": round(cap["aggregate_mlups"], 1)},
                        "status_counts": rep["status_counts"], "peak_active": rep["peak_active"],
-                       "peak_gb": round(rep["peak_bytes"] / 1e9, 2)}}
+                       "peak_gb": round(rep["peak_bytes"] / 1e9, 2),
+                       "steps_p50": rep["steps_p50"], "steps_p99": rep["steps_p99"],
+                       "final_residual_p50": rep["final_residual_p50"],
+                       "final_residual_p90": rep["final_residual_p90"],
+                       "p50_time_by_status_s": {k: round(v, 3) for k, v in rep["p50_time_by_status_s"].items()},
+                       "scheme": args.scheme}}
+    print(json.dumps(out), flush=True)
+
+
+def tilted_poiseuille(wl):
+    """eq. pois: v0 [1 - ((x - x0 - g (z - z0)) / dx)^2] along the channel axis, on the
+    fluid nodes of a tilted-channel workload (zero on solid nodes)."""
+    import numpy as np
+    m = wl.meta
+    x = np.arange(wl.nx)[None, None, :]
+    z = np.arange(wl.nz)[:, None, None]
+    d = (x - m["x0"] - m["gamma"] * (z - m["z0"])) / m["half_width"] + np.zeros((1, wl.ny, 1))
+    prof = np.where(wl.solid == 0, m["u0"] * (1 - d * d), 0.0)
+    return prof[None] * np.array(m["direction"])[:, None, None, None]
+
+
+def tilted_xi(wl, u):
+    """eq. deferr as the mean of |v - v^P| / |v^P| over the fluid nodes of the layers
+    within one channel width (20 nodes, times the scale) of the inflow and outflow
+    planes."""
+    import numpy as np
+    vp = tilted_poiseuille(wl)
+    z = np.arange(wl.nz)[:, None, None] + np.zeros((1, wl.ny, wl.nx))
+    w = 20 * wl.meta["scale"]
+    sel = (wl.solid == 0) & ((z < w) | (z >= wl.nz - w))
+    num = np.sqrt(((u - vp) ** 2).sum(0))[sel]
+    den = np.sqrt((vp ** 2).sum(0))[sel]
+    return float((num / den).mean())
+
+
+def study_tilted(args):
+    """The paper's tilted-channel comparison: xi of the on-site closure (GPU, FP64) at
+    the paper's size and at twice its resolution, of the straight channel, of the inflow
+    restricted to the plane normal, and of the N = 0 closure (FP64 oracle on the host:
+    a comparison closure the CUDA path does not carry)."""
+    import torch
+
+    import paper_0811_4593_gb300 as lbm
+    from paper_0811_4593_gb300 import build as lib_build
+    lib_build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cases = [("on_site", inp.tilted_channel(), 20000), ("on_site_2x", inp.tilted_channel(scale=2), 80000),
+             ("straight", inp.tilted_channel(shift=0), 20000),
+             ("normal_only", inp.tilted_channel(normal_only=True), 20000)]
+    out = {"study": "tilted channel (Sec. Numerical Results)", "tau": 1.0, "u0": 0.01, "xi": {}, "seconds": {}}
+    for name, wl, steps in cases:
+        t0 = time.perf_counter()
+        with lbm.Lattice.from_workload(wl, "f64") as lat:
+            lat.step(steps)
+            _, u = lat.macros()
+            u = u.cpu().numpy()
+        out["xi"][name] = round(tilted_xi(wl, u), 5)
+        out["seconds"][name] = round(time.perf_counter() - t0, 2)
+    if not args.no_cpu_baseline:
+        import oracle
+        wl = inp.tilted_channel()
+        t0 = time.perf_counter()
+        olat = oracle.Lattice.from_workload(wl)
+        f = oracle.run(olat, oracle.init_equilibrium(olat), 20000, form=oracle.FORM_COMPACT_NO_N)
+        _, u = oracle.macros(olat, f)
+        out["xi"]["n_zero_oracle"] = round(tilted_xi(wl, u), 5)
+        out["seconds"]["n_zero_oracle"] = round(time.perf_counter() - t0, 1)
+    out["paper"] = {"on_site": 0.0996, "n_zero": 0.126, "normal_only": 0.175, "on_site_2x": 0.051, "straight": 0.00235}
     print(json.dumps(out), flush=True)
 
 
@@ -470,17 +537,21 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true", help="run the serving mix instead of the sweep benchmark")
+    ap.add_argument("--study", choices=["tilted"], help="run a reproduction study instead of the benchmark")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--capacity-requests", type=int, default=200)
     ap.add_argument("--slots", type=int, default=512)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--max-steps", type=int, default=20000)
     ap.add_argument("--target", type=float, default=1e-8)
+    ap.add_argument("--scheme", choices=["ab", "aa"], default="ab", help="streaming scheme of the serving lattices")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         reference(args)
+    elif args.study == "tilted":
+        study_tilted(args)
     elif args.serving:
         serving(args)
     else:

@@ -169,6 +169,14 @@ LBM_API lbm_status lbm_macros(lbm_ctx* ctx, void* rho, void* u);
 LBM_API lbm_status lbm_set_populations(lbm_ctx* ctx, const void* src, int z0, int nzs, lbm_memory where);
 LBM_API lbm_status lbm_get_populations(lbm_ctx* ctx, void* dst, int z0, int nzs, lbm_memory where);
 
+/* Mark solid nodes: `solid` is a HOST array [nz][ny][nx], nonzero for a solid node
+ * (copied, not retained). Fluid nodes next to a solid node take the mid-grid
+ * bounce-back of Sec. "Boundary conditions" for the populations that would stream in
+ * from it: f_i(x) = f*_-i(x), the population the node sent towards the wall, reversed.
+ * Solid nodes keep their populations. Costs 4 bytes per node of extra traffic per step.
+ * A/B scheme only (LBM_ERR_ARG for AA). Synchronises. */
+LBM_API lbm_status lbm_set_solid(lbm_ctx* ctx, const uint8_t* solid);
+
 /* Block the host until the context's stream is idle; reports asynchronous errors. */
 LBM_API lbm_status lbm_sync(lbm_ctx* ctx);
 

@@ -81,6 +81,7 @@ class Workload:
     steps: int = 0
     meta: dict = field(default_factory=dict)
     ptabs: list = field(default_factory=lambda: [None] * 6)
+    solid: object = None  # optional (nz, ny, nx) uint8 mask of solid nodes
 
     @property
     def cells(self) -> int:
@@ -165,6 +166,43 @@ def pressure_duct(n=16, length=48, tau=1.0, rho_in=1.005, rho_out=0.995, steps=0
     return make_workload("pressure_duct", length, n, n, tau, [None, None, ZERO, ZERO, ZERO, ZERO], steps,
                          meta={"rho_in": rho_in, "rho_out": rho_out},
                          face_p=[rho_in, rho_out, None, None, None, None])
+
+
+def tilted_channel(scale: int = 1, tau: float = 1.0, u0: float = 0.01, shift: int = 40, normal_only=False,
+                   steps: int = 20000) -> Workload:
+    """The tilted-channel geometry of the paper's numerical results: a 64 x 8 x 128
+    domain (times ``scale``), periodic in x and y; a channel 20 nodes wide along x whose
+    centre line moves by ``shift`` nodes in x over the 127 node spacings in z (zero:
+    the straight channel); solid nodes outside it; the Poiseuille profile along the
+    channel axis prescribed on the fluid nodes of the planes z = 0 and z = nz - 1.
+
+    Fluid nodes satisfy |x - x_c(z)| < w/2 with x_c(z) = x0 + g (z - z0), (x0, z0) the
+    centre of the domain, g = shift / 127, w = 20 (all lengths times ``scale``). The
+    profile is v(x) = u0 [1 - ((x - x_c(z)) / (w/2))^2] along (g, 0, 1) / |(g, 0, 1)|
+    (eq. pois); ``normal_only`` keeps only its z component (the comparison inflow
+    restricted to the plane normal)."""
+    nx, ny, nz = 64 * scale, 8 * scale, 128 * scale
+    g = shift / 127.0
+    half = 10.0 * scale
+    x0, z0 = (nx - 1) / 2.0, (nz - 1) / 2.0
+    x = np.arange(nx)[None, None, :]
+    z = np.arange(nz)[:, None, None]
+    d = (x - x0 - g * (z - z0)) / half + 0.0 * np.zeros((1, ny, 1))
+    solid = (np.abs(d) >= 1.0).astype(np.uint8)
+    direction = np.array([g, 0.0, 1.0]) / math.hypot(g, 1.0)
+    prof = np.where(solid == 0, u0 * (1.0 - d * d), 0.0)          # [z][y][x]
+    vel = prof[..., None] * direction                               # [z][y][x][3]
+    if normal_only:
+        vel[..., 0] = 0.0
+        vel[..., 1] = 0.0
+    # z faces: tables [y][x][3]
+    bottom = np.ascontiguousarray(vel[0])
+    top = np.ascontiguousarray(vel[-1])
+    wl = make_workload("tilted_channel", nx, ny, nz, tau, [None, None, None, None, bottom, top], steps,
+                       meta={"u0": u0, "gamma": g, "half_width": half, "x0": x0, "z0": z0, "scale": scale,
+                             "direction": direction.tolist(), "normal_only": normal_only})
+    wl.solid = np.ascontiguousarray(solid)
+    return wl
 
 
 def random_pressure_workload(seed: int, nx: int, ny: int, nz: int, tau: float, periodic_y: bool = False,

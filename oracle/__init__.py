@@ -41,6 +41,10 @@ def lib():
         L.orc_stream.argtypes = [C.c_int] * 3 + [_ip, _dp, _dp]
         L.orc_step.argtypes = [C.c_int] * 3 + [_ip, C.c_void_p, C.c_void_p, C.c_double, _dp, _dp, C.c_int]
         L.orc_run.argtypes = [C.c_int] * 3 + [_ip, C.c_void_p, C.c_void_p, C.c_double, C.c_int, _dp, _dp, C.c_int]
+        L.orc_step_geom.argtypes = [C.c_int] * 3 + [_ip, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, _dp, _dp,
+                                                    C.c_int]
+        L.orc_run_geom.argtypes = [C.c_int] * 3 + [_ip, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                                                   _dp, _dp, C.c_int]
         L.orc_init_equilibrium.argtypes = [C.c_int] * 3 + [C.c_double, _dp]
         L.orc_macros.argtypes = [C.c_int] * 3 + [_dp, _dp, _dp]
         L.orc_reduce.argtypes = [C.c_int] * 3 + [_dp, C.c_void_p, _dp]
@@ -50,7 +54,7 @@ def lib():
         L.orc_lattice.argtypes = [_ip, _dp, _ip]
         L.orc_threads.restype = C.c_int
         for name in ("orc_close_face", "orc_close_edge", "orc_close_corner", "orc_close_face_pressure", "orc_stream",
-                     "orc_step", "orc_run", "orc_sources", "orc_update_gathered"):
+                     "orc_step", "orc_run", "orc_step_geom", "orc_run_geom", "orc_sources", "orc_update_gathered"):
             getattr(L, name).restype = C.c_int
         _LIB = L
     return _LIB
@@ -128,9 +132,10 @@ class Lattice:
     shape (n2, n1, 3) over the face's two tangential axes in increasing axis order (the
     prescribed velocity; for a pressure face its tangential part), or None for a
     periodic face. ``ptabs[i]`` is the (n2, n1) prescribed density of a pressure face.
+    ``solid`` is an optional (nz, ny, nx) mask of solid nodes (mid-grid bounce-back).
     """
 
-    def __init__(self, nx, ny, nz, kinds, utabs, tau, ptabs=None):
+    def __init__(self, nx, ny, nz, kinds, utabs, tau, ptabs=None, solid=None):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.kinds = np.ascontiguousarray(kinds, np.int32)
         self.tau = float(tau)
@@ -151,10 +156,18 @@ class Lattice:
                 pptrs[i] = pt.ctypes.data
         self._ptrs = ptrs
         self._pptrs = pptrs
+        self.solid = None if solid is None else np.ascontiguousarray(solid, np.uint8)
+        if self.solid is not None and self.solid.shape != (self.nz, self.ny, self.nx):
+            raise ValueError("solid mask must be (nz, ny, nx)")
+
+    @property
+    def _solid_ptr(self):
+        return None if self.solid is None else self.solid.ctypes.data
 
     @classmethod
     def from_workload(cls, wl):
-        return cls(wl.nx, wl.ny, wl.nz, wl.kinds, wl.utabs, wl.tau, getattr(wl, "ptabs", None))
+        return cls(wl.nx, wl.ny, wl.nz, wl.kinds, wl.utabs, wl.tau, getattr(wl, "ptabs", None),
+                   getattr(wl, "solid", None))
 
     @property
     def shape(self):
@@ -181,18 +194,24 @@ def stream(lat: Lattice, f) -> np.ndarray:
     return out
 
 
+# closure forms: 0 explicit per-plane formulas, 1 compact rule, 3 the compact rule with
+# the transverse corrections forced to zero (the paper's N = 0 comparison closure)
+FORM_EXPLICIT, FORM_COMPACT, FORM_COMPACT_NO_N = 0, 1, 3
+
+
 def step(lat: Lattice, f, form: int = 0) -> np.ndarray:
     fin = np.ascontiguousarray(f, np.float64)
     out = np.zeros(lat.shape)
-    _check(lib().orc_step(*lat.dims(), lat.kinds, lat._ptrs, lat._pptrs, lat.tau, fin, out, form), "step")
+    _check(lib().orc_step_geom(*lat.dims(), lat.kinds, lat._ptrs, lat._pptrs, lat._solid_ptr, lat.tau, fin, out,
+                               form), "step")
     return out
 
 
 def run(lat: Lattice, f, nsteps: int, form: int = 0) -> np.ndarray:
     g = np.array(f, np.float64, order="C")
     work = np.empty_like(g)
-    _check(lib().orc_run(*lat.dims(), lat.kinds, lat._ptrs, lat._pptrs, lat.tau, int(nsteps), g, work, form),
-           "run")
+    _check(lib().orc_run_geom(*lat.dims(), lat.kinds, lat._ptrs, lat._pptrs, lat._solid_ptr, lat.tau, int(nsteps),
+                              g, work, form), "run")
     return g
 
 

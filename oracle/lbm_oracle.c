@@ -224,7 +224,10 @@ static double close_back(double* f, const double* v, double rho_fixed) {
  *   f_-i = f_i - 6 w_i rho c_i.v - (rho/3) t_i.v + 1/2 sum_j f_j (t_i.c_j)(1 - |c_j.n|)
  * with t_i = c_i - (c_i.n) n and rho from the plane's density relation (eq. uin).
  * -------------------------------------------------------------------------------- */
-static double close_face_compact(double* f, int face, const double* v, double rho_fixed) {
+/* zero_n != 0 is the comparison closure of the paper's Fig. (vdifffields) b: the same
+ * non-equilibrium bounce-back with the transverse corrections N forced to zero
+ * (eqs. f9NoNs-f17NoNs), used only to reproduce that comparison. */
+static double close_face_compact(double* f, int face, const double* v, double rho_fixed, int zero_n) {
   int n[3];
   face_normal(face, n);
   /* density: in-plane populations once, outgoing ones twice, unknown ones not at all */
@@ -248,13 +251,16 @@ static double close_face_compact(double* f, int face, const double* v, double rh
       double tc = t[0] * CV[j][0] + t[1] * CV[j][1] + t[2] * CV[j][2];
       corr += f[j] * tc;
     }
-    f[opposite(k)] = f[k] - 6.0 * WT[k] * rho * dot_cv(k, v) - rho / 3.0 * tv + 0.5 * corr;
+    if (zero_n) f[opposite(k)] = f[k] - 6.0 * WT[k] * rho * dot_cv(k, v);
+    else f[opposite(k)] = f[k] - 6.0 * WT[k] * rho * dot_cv(k, v) - rho / 3.0 * tv + 0.5 * corr;
   }
   return rho;
 }
 
+/* form: bit 0 set = compact rule, else the explicit per-plane formulas; bit 1 set = the
+ * N = 0 comparison closure (compact rule only). */
 static double close_face_form(int face, int form, double* f, const double* v, double rho_fixed) {
-  if (form == 1) return close_face_compact(f, face, v, rho_fixed);
+  if (form & 1) return close_face_compact(f, face, v, rho_fixed, form & 2);
   switch (face) {
     case 0: return close_left(f, v, rho_fixed);
     case 1: return close_right(f, v, rho_fixed);
@@ -323,7 +329,7 @@ static double pressure_velocity_compact(int face, const double* f, double rho0) 
 int orc_close_face_pressure(int face, int form, double* f, double rho0, const double* v, double* vn_out) {
   if (face < 0 || face > 5 || !(rho0 > 0.0)) return ORC_ERR_ARG;
   double u[3] = {v[0], v[1], v[2]};
-  double vn = form == 1 ? pressure_velocity_compact(face, f, rho0) : pressure_velocity_explicit(face, f, rho0);
+  double vn = (form & 1) ? pressure_velocity_compact(face, f, rho0) : pressure_velocity_explicit(face, f, rho0);
   u[face / 2] = vn;
   close_face_form(face, form, f, u, rho0);
   if (vn_out) *vn_out = vn;
@@ -425,6 +431,7 @@ typedef struct {
   const double* utab[6];  /* [n2][n1][3] per velocity or pressure face (pressure: the
                              tangential velocity; the normal component is ignored) */
   const double* ptab[6];  /* [n2][n1] prescribed density per pressure face */
+  const unsigned char* solid; /* optional [nz][ny][nx]: nonzero marks a solid node */
   double tau;
 } lattice_t;
 
@@ -512,12 +519,27 @@ static int update_node(const lattice_t* L, int x, int y, int z, double* f, int f
 static int make_lattice(lattice_t* L, int nx, int ny, int nz, const int* kind, const double* const* utab,
                         const double* const* ptab, double tau) {
   L->nx = nx; L->ny = ny; L->nz = nz; L->tau = tau;
+  L->solid = NULL;
   for (int i = 0; i < 6; ++i) {
     L->kind[i] = kind[i];
     L->utab[i] = utab ? utab[i] : NULL;
     L->ptab[i] = ptab ? ptab[i] : NULL;
   }
   return lattice_check(L);
+}
+
+/* Flat index (population * N + node) that population k of node (x,y,z) takes its
+ * streamed value from, or -1 when unknown. Pull streaming (Sec. "Simulation method"):
+ * population k of node x - c_k. Next to a solid node the mid-grid bounce-back of
+ * Sec. "Boundary conditions" applies instead: the population that node x sent towards
+ * the solid node returns reversed, i.e. population -k of node x itself. */
+static int64_t gather_source(const lattice_t* L, int x, int y, int z, int k) {
+  int64_t N = (int64_t)L->nx * L->ny * L->nz;
+  int64_t node = ((int64_t)z * L->ny + y) * L->nx + x;
+  int64_t s = pull_source(L, x, y, z, k);
+  if (s < 0) return -1;
+  if (L->solid && L->solid[s]) return (int64_t)opposite(k) * N + node;
+  return (int64_t)k * N + s;
 }
 
 /* Pull streaming only: out[k][node] = in[k][node - c_k], NaN where unknown. */
@@ -541,11 +563,14 @@ int orc_stream(int nx, int ny, int nz, const int* kind, const double* fin, doubl
 }
 
 /* One time step fin -> fout (streaming, closure, collision). */
-int orc_step(int nx, int ny, int nz, const int* kind, const double* const* utab, const double* const* ptab,
-             double tau, const double* fin, double* fout, int form) {
+/* One time step fin -> fout (streaming, closure, collision). Solid nodes (when a mask
+ * is given) keep their populations unchanged. */
+int orc_step_geom(int nx, int ny, int nz, const int* kind, const double* const* utab, const double* const* ptab,
+                  const unsigned char* solid, double tau, const double* fin, double* fout, int form) {
   lattice_t L;
   int rc = make_lattice(&L, nx, ny, nz, kind, utab, ptab, tau);
   if (rc) return rc;
+  L.solid = solid;
   int64_t N = (int64_t)nx * ny * nz;
   int err = 0;
 #pragma omp parallel for schedule(static) reduction(| : err)
@@ -554,9 +579,13 @@ int orc_step(int nx, int ny, int nz, const int* kind, const double* const* utab,
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
         int64_t node = ((int64_t)z * ny + y) * nx + x;
+        if (solid && solid[node]) {
+          for (int k = 0; k < Q; ++k) fout[k * N + node] = fin[k * N + node];
+          continue;
+        }
         for (int k = 0; k < Q; ++k) {
-          int64_t s = pull_source(&L, x, y, z, k);
-          f[k] = (s < 0) ? NAN : fin[k * N + s];
+          int64_t s = gather_source(&L, x, y, z, k);
+          f[k] = (s < 0) ? NAN : fin[s];
         }
         err |= update_node(&L, x, y, z, f, form);
         for (int k = 0; k < Q; ++k) fout[k * N + node] = f[k];
@@ -565,19 +594,29 @@ int orc_step(int nx, int ny, int nz, const int* kind, const double* const* utab,
   return err;
 }
 
+int orc_step(int nx, int ny, int nz, const int* kind, const double* const* utab, const double* const* ptab,
+             double tau, const double* fin, double* fout, int form) {
+  return orc_step_geom(nx, ny, nz, kind, utab, ptab, NULL, tau, fin, fout, form);
+}
+
 /* nsteps time steps; f holds the initial and the final state, work is scratch of the
  * same size. */
-int orc_run(int nx, int ny, int nz, const int* kind, const double* const* utab, const double* const* ptab,
-            double tau, int nsteps, double* f, double* work, int form) {
+int orc_run_geom(int nx, int ny, int nz, const int* kind, const double* const* utab, const double* const* ptab,
+                 const unsigned char* solid, double tau, int nsteps, double* f, double* work, int form) {
   int64_t n = (int64_t)Q * nx * ny * nz;
   double *a = f, *b = work;
   for (int s = 0; s < nsteps; ++s) {
-    int rc = orc_step(nx, ny, nz, kind, utab, ptab, tau, a, b, form);
+    int rc = orc_step_geom(nx, ny, nz, kind, utab, ptab, solid, tau, a, b, form);
     if (rc) return rc;
     double* t = a; a = b; b = t;
   }
   if (a != f) memcpy(f, a, (size_t)n * sizeof(double));
   return ORC_OK;
+}
+
+int orc_run(int nx, int ny, int nz, const int* kind, const double* const* utab, const double* const* ptab,
+            double tau, int nsteps, double* f, double* work, int form) {
+  return orc_run_geom(nx, ny, nz, kind, utab, ptab, NULL, tau, nsteps, f, work, form);
 }
 
 /* f = f_eq(rho0, 0) on every node (the initial, post-collision state). */

@@ -39,6 +39,7 @@ EXPORTS = {
     "lbm_set_populations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "lbm_get_populations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "lbm_sync": (C.c_int, [C.c_void_p]),
+    "lbm_set_solid": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_info": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_batch_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
@@ -227,10 +228,18 @@ class Lattice:
         self._ctx = out
         check(lib().lbm_set_stream(self._ctx, C.c_void_p(self.stream.cuda_stream)), self._ctx)
 
+    def set_solid(self, solid):
+        """Mark solid nodes (uint8 (nz, ny, nx), nonzero = solid): mid-grid bounce-back
+        walls; A/B scheme only."""
+        m = np.ascontiguousarray(solid, np.uint8)
+        if m.shape != (self.nz, self.ny, self.nx):
+            raise ValueError(f"solid mask shape {m.shape} != {(self.nz, self.ny, self.nx)}")
+        check(lib().lbm_set_solid(self.ctx, C.c_void_p(m.ctypes.data)), self.ctx)
+
     @classmethod
     def from_workload(cls, wl, precision="f32", **kw):
         """A lattice for any object with nx, ny, nz, tau, rho0, kinds, utabs (and ptabs
-        for pressure faces)."""
+        for pressure faces, solid for solid nodes)."""
         ptabs = getattr(wl, "ptabs", None) or [None] * 6
         faces = []
         for k, t, p in zip(wl.kinds, wl.utabs, ptabs):
@@ -240,7 +249,10 @@ class Lattice:
                 faces.append(Pressure(p, t))
             else:
                 faces.append(t)
-        return cls(wl.nx, wl.ny, wl.nz, wl.tau, faces, precision, wl.rho0, **kw)
+        lat = cls(wl.nx, wl.ny, wl.nz, wl.tau, faces, precision, wl.rho0, **kw)
+        if getattr(wl, "solid", None) is not None:
+            lat.set_solid(wl.solid)
+        return lat
 
     # -- lifetime -------------------------------------------------------------------
     def close(self):

@@ -521,25 +521,43 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
       const uint32_t sz = cz(k) > 0 ? zm : (cz(k) < 0 ? zp : z);
       return (sz * a.ny + sy) * a.nx + sx;
     };
+    // solid-node links (A/B lattices with solid nodes only; 0 everywhere else)
+    const uint32_t lm = (MODE == STREAM_AB && a.links) ? __ldg(a.links + cell) : 0u;
     T h[Q];
-    static_for<0, Q>([&](auto kc) {
-      constexpr int k = decltype(kc)::value;
-      if constexpr (MODE == STREAM_AB) {
-        h[k] = Storage<S>::load(static_cast<const S*>(a.src_pop[k]) + pull_idx(kc));
-      } else if constexpr (MODE == STREAM_AA_GATHER) {
-        h[k] = Storage<S>::load(static_cast<const S*>(a.src_pop[opp(k)]) + pull_idx(kc));
-      } else {
-        h[k] = Storage<S>::load(static_cast<const S*>(a.src_pop[k]) + cell);
-      }
-    });
+    if (lm == 0u) {
+      static_for<0, Q>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        if constexpr (MODE == STREAM_AB) {
+          h[k] = Storage<S>::load(static_cast<const S*>(a.src_pop[k]) + pull_idx(kc));
+        } else if constexpr (MODE == STREAM_AA_GATHER) {
+          h[k] = Storage<S>::load(static_cast<const S*>(a.src_pop[opp(k)]) + pull_idx(kc));
+        } else {
+          h[k] = Storage<S>::load(static_cast<const S*>(a.src_pop[k]) + cell);
+        }
+      });
+    } else {
+      // a solid node keeps its populations; next to a solid node the population that
+      // would come from it is the node's own population -k reversed (mid-grid
+      // bounce-back, Sec. "Boundary conditions")
+      static_for<0, Q>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        const bool own = (lm & SOLID_NODE) != 0u;
+        const bool back = (lm >> k) & 1u;
+        const S* p = own ? static_cast<const S*>(a.src_pop[k]) + cell
+                         : (back ? static_cast<const S*>(a.src_pop[opp(k)]) + cell
+                                 : static_cast<const S*>(a.src_pop[k]) + pull_idx(kc));
+        h[k] = Storage<S>::load(p);
+      });
+    }
+    const bool solid = (lm & SOLID_NODE) != 0u;
     const int fx = px ? 0 : (x == 0 ? 1 : (x == a.nx - 1 ? 2 : 0));
     const int fy = py ? 0 : (y == 0 ? 1 : (y == a.ny - 1 ? 2 : 0));
     const int fz = pz ? 0 : (z == 0 ? 1 : (z == a.nz - 1 ? 2 : 0));
     const int code = fx + 3 * fy + 9 * fz;
-    if (code != 0) apply_boundary(code, a, x, y, z, h);
+    if (code != 0 && !solid) apply_boundary(code, a, x, y, z, h);
     const Moments<T> m = moments(h, rho0_of<T>(a));
     if constexpr (RESID) residual_terms(m, ref_rho<S>(a.rho0), static_cast<T*>(a.snap), a.N, cell, red);
-    collide(h, m, omega_of<T>(a));
+    if (!solid) collide(h, m, omega_of<T>(a));
     static_for<0, Q>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
       if constexpr (MODE == STREAM_AB) {

@@ -65,7 +65,11 @@ struct SweepArgs {
   FaceBC face[6];
   void* snap;         // residual steps: [3][N] velocity snapshot in the compute type
   double* partials;   // residual steps: [blocks][4] per-block sums
+  const uint32_t* links;  // optional [N]: bit k = the pull source of population k is
+                          // solid, bit 31 = the node is solid (nullptr: no solid nodes)
 };
+
+constexpr uint32_t SOLID_NODE = 1u << 31;
 
 // One lattice of a batch, as the batched sweep reads it from device memory.
 struct BatchEntry {

@@ -546,6 +546,52 @@ lbm_status lbm_get_populations(lbm_ctx* ctx, void* dst, int z0, int nzs, lbm_mem
   return copy_populations(ctx, dst, z0, nzs, where, false);
 }
 
+lbm_status lbm_set_solid(lbm_ctx* ctx, const uint8_t* solid) {
+  if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+  if (!solid) return fail(ctx, LBM_ERR_ARG, "solid is NULL");
+  if (ctx->scheme != LBM_SCHEME_AB) return fail(ctx, LBM_ERR_ARG, "solid nodes need the A/B scheme");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, LBM_ERR_CUDA, "cannot make device %d current", ctx->device);
+  if (lbm_status st0 = settle(ctx); st0 != LBM_OK) return st0;
+  // bit k: the node population k is pulled from (x - c_k, wrapped on periodic axes) is
+  // solid; bit 31: the node is solid. Sources outside a walled axis stay unflagged (the
+  // boundary closure fills those populations).
+  const int nx = ctx->nx, ny = ctx->ny, nz = ctx->nz;
+  const uint32_t per = ctx->args.periodic;
+  std::vector<uint32_t> links(ctx->N, 0u);
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const size_t node = (size_t(z) * ny + y) * nx + x;
+        uint32_t m = solid[node] ? lbm::SOLID_NODE : 0u;
+        for (int k = 0; k < 19; ++k) {
+          int p[3] = {x - lbm::cx(k), y - lbm::cy(k), z - lbm::cz(k)};
+          const int dims[3] = {nx, ny, nz};
+          bool inside = true;
+          for (int a = 0; a < 3; ++a) {
+            if (p[a] < 0 || p[a] >= dims[a]) {
+              if (!((per >> a) & 1u)) inside = false;
+              p[a] = (p[a] % dims[a] + dims[a]) % dims[a];
+            }
+          }
+          if (inside && solid[(size_t(p[2]) * ny + p[1]) * nx + p[0]]) m |= 1u << k;
+        }
+        links[node] = m;
+      }
+  if (!ctx->args.links) {
+    void* d = ctx_alloc(ctx, sizeof(uint32_t) * ctx->N);
+    if (!d) return fail(ctx, LBM_ERR_OOM, "allocation of the solid-link mask failed");
+    ctx->args.links = static_cast<const uint32_t*>(d);
+  }
+  LBM_CUDA(ctx, cudaMemcpyAsync(const_cast<uint32_t*>(ctx->args.links), links.data(), sizeof(uint32_t) * ctx->N,
+                                cudaMemcpyHostToDevice, ctx->stream), "uploading the solid-link mask");
+  // solid nodes are carried unchanged from buffer to buffer: start both alike
+  LBM_CUDA(ctx, cudaMemcpyAsync(ctx->buf[ctx->cur ^ 1], ctx->buf[ctx->cur], 19ull * ctx->N * storage_bytes(ctx->prec),
+                                cudaMemcpyDeviceToDevice, ctx->stream), "copying the state");
+  LBM_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "synchronising");
+  return LBM_OK;
+}
+
 lbm_status lbm_sync(lbm_ctx* ctx) {
   if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
   DeviceGuard g(ctx->device);

@@ -24,13 +24,15 @@ STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
 COMPUTE_BYTES = {"f64": 8, "f32": 4, "f16": 4}
 
 
-def footprint_bytes(nx: int, ny: int, nz: int, precision: str) -> int:
-    """Device bytes one resident lattice holds: two population buffers, the residual
-    snapshot and partial sums, the face tables and the reduction scalars."""
+def footprint_bytes(nx: int, ny: int, nz: int, precision: str, scheme: str = "ab") -> int:
+    """Device bytes one resident lattice holds: its population buffers (two for the A/B
+    scheme, one for AA), the residual snapshot and partial sums, the face tables and the
+    reduction scalars."""
     n = nx * ny * nz
     blocks = (n + 255) // 256
     faces = 2 * (ny * nz + nx * nz + nx * ny) * 48
-    return 2 * 19 * STORAGE_BYTES[precision] * n + 3 * COMPUTE_BYTES[precision] * n + 32 * blocks + faces + 32
+    buffers = 1 if scheme == "aa" else 2
+    return buffers * 19 * STORAGE_BYTES[precision] * n + 3 * COMPUTE_BYTES[precision] * n + 32 * blocks + faces + 32
 
 
 @dataclass
@@ -86,7 +88,7 @@ def percentile(values, q):
 class Server:
     def __init__(self, precision: str = "f32", capacity: int = 256, budget_bytes: float = 150e9,
                  round_steps: int = 100, max_steps: int = 20000, target: float = 1e-8, plateau_checks: int = 10,
-                 keep_populations: bool = False):
+                 plateau_ceiling: float = 1e-5, keep_populations: bool = False, scheme: str = "ab"):
         self.precision = precision
         self.capacity = int(capacity)
         self.budget = float(budget_bytes)
@@ -94,7 +96,9 @@ class Server:
         self.max_steps = int(max_steps)
         self.target = float(target)
         self.plateau = int(plateau_checks)
+        self.plateau_ceiling = float(plateau_ceiling)
         self.keep_populations = keep_populations
+        self.scheme = scheme
 
     def serve(self, jobs, closed_loop: bool = False, clock=time.perf_counter, idle_sleep=0.001):
         """Run every job to completion. ``closed_loop`` ignores arrival times (all jobs
@@ -119,13 +123,13 @@ class Server:
                 free = batch.free_slots()
                 while waiting and free:
                     wl = waiting[0].workload
-                    need = footprint_bytes(wl.nx, wl.ny, wl.nz, self.precision)
+                    need = footprint_bytes(wl.nx, wl.ny, wl.nz, self.precision, self.scheme)
                     if need > self.budget:
                         raise ValueError(f"job {waiting[0].jid} needs {need} bytes, more than the whole budget")
                     if used + need > self.budget:
                         break
                     job = waiting.popleft()
-                    lat = Lattice.from_workload(job.workload, self.precision)
+                    lat = Lattice.from_workload(job.workload, self.precision, scheme=self.scheme)
                     slot = free.pop(0)
                     batch.attach(slot, lat)
                     active[slot] = _Active(job, lat, clock() - t0, need)
@@ -156,7 +160,7 @@ class Server:
                             a.best, a.since_best = r, 0
                         else:
                             a.since_best += 1
-                        if a.since_best >= self.plateau:
+                        if a.best < self.plateau_ceiling and a.since_best >= self.plateau:
                             status = "plateau"
                         elif a.steps >= self.max_steps:
                             status = "step_cap"
@@ -175,6 +179,10 @@ class Server:
             batch.close()
         wall = clock() - t0
         tts = [r.time_to_steady_s for r in results]
+        ok = [r for r in results if r.status != "diverged"]
+        by_status = collections.defaultdict(list)
+        for r in results:
+            by_status[r.status].append(r.time_to_steady_s)
         report = {
             "jobs": len(results),
             "wall_s": wall,
@@ -185,6 +193,11 @@ class Server:
             "p50_time_to_steady_s": percentile(tts, 50),
             "p99_time_to_steady_s": percentile(tts, 99),
             "status_counts": dict(collections.Counter(r.status for r in results)),
+            "p50_time_by_status_s": {k: percentile(v, 50) for k, v in by_status.items()},
+            "steps_p50": percentile([r.steps for r in results], 50),
+            "steps_p99": percentile([r.steps for r in results], 99),
+            "final_residual_p50": percentile([r.residual for r in ok], 50),
+            "final_residual_p90": percentile([r.residual for r in ok], 90),
             "peak_active": peak_active,
             "peak_bytes": peak_bytes,
         }
