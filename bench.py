@@ -445,15 +445,17 @@ def tilted_poiseuille(wl):
     return prof[None] * np.array(m["direction"])[:, None, None, None]
 
 
-def tilted_xi(wl, u):
-    """eq. deferr as the mean of |v - v^P| / |v^P| over the fluid nodes of the layers
-    within one channel width (20 nodes, times the scale) of the inflow and outflow
-    planes."""
+def tilted_xi(wl, u, near_planes: bool = False):
+    """eq. deferr as the mean of |v - v^P| / |v^P| over fluid nodes: all of them, or
+    (near_planes) those within one channel width (20 nodes, times the scale) of the
+    inflow and outflow planes -- the two readings of the paper's averaging volume."""
     import numpy as np
     vp = tilted_poiseuille(wl)
-    z = np.arange(wl.nz)[:, None, None] + np.zeros((1, wl.ny, wl.nx))
-    w = 20 * wl.meta["scale"]
-    sel = (wl.solid == 0) & ((z < w) | (z >= wl.nz - w))
+    sel = wl.solid == 0
+    if near_planes:
+        z = np.arange(wl.nz)[:, None, None] + np.zeros((1, wl.ny, wl.nx))
+        w = 20 * wl.meta["scale"]
+        sel = sel & ((z < w) | (z >= wl.nz - w))
     num = np.sqrt(((u - vp) ** 2).sum(0))[sel]
     den = np.sqrt((vp ** 2).sum(0))[sel]
     return float((num / den).mean())
@@ -473,7 +475,8 @@ def study_tilted(args):
     cases = [("on_site", inp.tilted_channel(), 20000), ("on_site_2x", inp.tilted_channel(scale=2), 80000),
              ("straight", inp.tilted_channel(shift=0), 20000),
              ("normal_only", inp.tilted_channel(normal_only=True), 20000)]
-    out = {"study": "tilted channel (Sec. Numerical Results)", "tau": 1.0, "u0": 0.01, "xi": {}, "seconds": {}}
+    out = {"study": "tilted channel (Sec. Numerical Results)", "tau": 1.0, "u0": 0.01,
+           "xi": {}, "xi_near_planes": {}, "seconds": {}}
     for name, wl, steps in cases:
         t0 = time.perf_counter()
         with lbm.Lattice.from_workload(wl, "f64") as lat:
@@ -481,6 +484,7 @@ def study_tilted(args):
             _, u = lat.macros()
             u = u.cpu().numpy()
         out["xi"][name] = round(tilted_xi(wl, u), 5)
+        out["xi_near_planes"][name] = round(tilted_xi(wl, u, near_planes=True), 5)
         out["seconds"][name] = round(time.perf_counter() - t0, 2)
     if not args.no_cpu_baseline:
         import oracle
@@ -490,9 +494,56 @@ def study_tilted(args):
         f = oracle.run(olat, oracle.init_equilibrium(olat), 20000, form=oracle.FORM_COMPACT_NO_N)
         _, u = oracle.macros(olat, f)
         out["xi"]["n_zero_oracle"] = round(tilted_xi(wl, u), 5)
+        out["xi_near_planes"]["n_zero_oracle"] = round(tilted_xi(wl, u, near_planes=True), 5)
         out["seconds"]["n_zero_oracle"] = round(time.perf_counter() - t0, 1)
     out["paper"] = {"on_site": 0.0996, "n_zero": 0.126, "normal_only": 0.175, "on_site_2x": 0.051, "straight": 0.00235}
     print(json.dumps(out), flush=True)
+
+
+def study_duct(args):
+    """The paper's square-channel study: pressure planes at both ends of an n x n duct
+    with no-slip walls, edges and corners; relative L2 error of the mid-duct velocity
+    against eq. squarechannel (50 terms, local pressure gradient, eta from eq. visc)
+    for widths 8 .. 64 (FP64, on the GPU)."""
+    import numpy as np
+    import torch
+
+    import paper_0811_4593_gb300 as lbm
+    from paper_0811_4593_gb300 import build as lib_build
+    lib_build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+
+    def series(n, terms=50):
+        b = n - 1.0
+        s_ = np.arange(n) - (n - 1) / 2.0
+        X, Y = np.meshgrid(s_, s_, indexing="ij")
+        C = np.zeros_like(X)
+        for m in range(terms):
+            k = 2 * m + 1
+            C += (-1) ** m * np.cosh(k * np.pi * X / b) * np.cos(k * np.pi * Y / b) / (k ** 3 * np.cosh(k * np.pi / 2))
+        return b * b / 4 - Y ** 2 - C * 8 * b * b / np.pi ** 3
+
+    rows = []
+    for n in (9, 13, 17, 25, 33, 49, 65):
+        length = 3 * n
+        wl = inp.pressure_duct(n, length, 1.0, 1.002, 0.998)
+        t0 = time.perf_counter()
+        with lbm.Lattice.from_workload(wl, "f64") as lat:
+            lat.step(14 * n * n)
+            rho, u = lat.macros()
+            rho, u = rho.cpu().numpy(), u.cpu().numpy()
+        xm = length // 2
+        grad = (rho[:, :, xm + 1].mean() - rho[:, :, xm - 1].mean()) / 2.0 / 3.0
+        eta = rho[:, :, xm].mean() * 0.5 / 3.0
+        an = -grad / (2 * eta) * series(n)
+        err = float(np.sqrt(((u[0][:, :, xm] - an) ** 2).mean() / (an ** 2).mean()))
+        rows.append({"width": n - 1, "nodes": wl.cells, "steps": 14 * n * n, "l2_rel_error": err,
+                     "seconds": round(time.perf_counter() - t0, 2)})
+    for i in range(1, len(rows)):
+        rows[i]["slope"] = round(float(np.log(rows[i - 1]["l2_rel_error"] / rows[i]["l2_rel_error"]) /
+                                       np.log(rows[i]["width"] / rows[i - 1]["width"])), 3)
+    print(json.dumps({"study": "pressure-driven square duct (Sec. Numerical Results)", "tau": 1.0,
+                      "rho_in_out": [1.002, 0.998], "rows": rows, "paper_slope": 2}), flush=True)
 
 
 def reference(args):
@@ -537,7 +588,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true", help="run the serving mix instead of the sweep benchmark")
-    ap.add_argument("--study", choices=["tilted"], help="run a reproduction study instead of the benchmark")
+    ap.add_argument("--study", choices=["tilted", "duct"], help="run a reproduction study instead of the benchmark")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--capacity-requests", type=int, default=200)
     ap.add_argument("--slots", type=int, default=512)
@@ -552,6 +603,8 @@ def main():
         reference(args)
     elif args.study == "tilted":
         study_tilted(args)
+    elif args.study == "duct":
+        study_duct(args)
     elif args.serving:
         serving(args)
     else:

@@ -82,6 +82,8 @@ class Workload:
     meta: dict = field(default_factory=dict)
     ptabs: list = field(default_factory=lambda: [None] * 6)
     solid: object = None  # optional (nz, ny, nx) uint8 mask of solid nodes
+    code: object = None   # optional (nz, ny, nx) int8 on-site boundary rule codes
+    force: object = None  # optional body force (3,)
 
     @property
     def cells(self) -> int:
@@ -202,6 +204,183 @@ def tilted_channel(scale: int = 1, tau: float = 1.0, u0: float = 0.01, shift: in
                        meta={"u0": u0, "gamma": g, "half_width": half, "x0": x0, "z0": z0, "scale": scale,
                              "direction": direction.tolist(), "normal_only": normal_only})
     wl.solid = np.ascontiguousarray(solid)
+    return wl
+
+
+# ------------------------------------------------------------------------------------
+# General geometries: per-node boundary codes (the normal stored on the node as a
+# lattice-vector index, as the C ABI defines them) and body forces.
+# ------------------------------------------------------------------------------------
+
+# The paper's lattice vectors c_1..c_18 (columns of its matrix M); a code names a
+# normal by its index here.
+PAPER_VECTORS = ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+                 (1, 1, 0), (1, -1, 0), (1, 0, 1), (1, 0, -1), (-1, 1, 0), (-1, -1, 0),
+                 (-1, 0, 1), (-1, 0, -1), (0, 1, 1), (0, 1, -1), (0, -1, 1), (0, -1, -1))
+
+
+def vector_index(v) -> int:
+    """Paper index (1..18) of a lattice vector."""
+    return PAPER_VECTORS.index(tuple(int(a) for a in v)) + 1
+
+
+def plane_code(n) -> int:
+    return vector_index(n)
+
+
+def concave_edge_code(n1, n2) -> int:
+    return vector_index(np.add(n1, n2))
+
+
+def convex_edge_code(n1, n2) -> int:
+    return -vector_index(np.add(n1, n2))
+
+
+def corner_code(n) -> int:
+    sx, sy, sz = (int(a) for a in n)
+    return 19 + (sx < 0) + 2 * (sy < 0) + 4 * (sz < 0)
+
+
+def junction_code(n_plane, n1, n2) -> int:
+    """Convex edge with plane normals n1, n2 meeting the plane with normal n_plane."""
+    p = vector_index(n_plane)
+    d = tuple(int(a) for a in np.add(n1, n2))
+    perp = [v for v in PAPER_VECTORS[6:] if sum(a * b for a, b in zip(v, n_plane)) == 0]
+    return 27 + 4 * (p - 1) + perp.index(d)
+
+
+def _axis_vec(a: int, s: int):
+    v = [0, 0, 0]
+    v[a] = s
+    return v
+
+
+def force_poiseuille(n: int = 32, tau: float = 2.0, force: float = 1e-5, wall_axis: int = 0, flow_axis: int = 2,
+                     other: int = 3, steps: int = 0) -> Workload:
+    """Plane Poiseuille flow driven by a body force (the paper's 32^3 check): resting
+    walls on both faces of ``wall_axis`` (n nodes, walls on the end nodes), periodic
+    on the other axes (``other`` nodes each, except ``n`` on the flow axis when other
+    is None), force along ``flow_axis``."""
+    dims = [other if other is not None else n] * 3
+    dims[wall_axis] = n
+    face_u = [None] * 6
+    face_u[2 * wall_axis] = ZERO
+    face_u[2 * wall_axis + 1] = ZERO
+    wl = make_workload("force_poiseuille", dims[0], dims[1], dims[2], tau, face_u, steps,
+                       meta={"wall_axis": wall_axis, "flow_axis": flow_axis, "force": force})
+    f = np.zeros(3)
+    f[flow_axis] = force
+    wl.force = f
+    return wl
+
+
+def embedded_walls(wl: Workload) -> Workload:
+    """The same lattice with its walled faces moved inside the domain: one layer of
+    solid nodes is added beyond every walled face, and the former boundary nodes carry
+    the codes of the planes, concave edges and corners they lie on. All walls of ``wl``
+    must be at rest (no-slip)."""
+    nx, ny, nz = wl.dims
+    walled = [wl.kinds[2 * a] != PERIODIC for a in range(3)]
+    for i in range(6):
+        if wl.kinds[i] == PRESSURE or (wl.kinds[i] == VELOCITY and np.any(wl.utabs[i] != 0.0)):
+            raise ValueError("embedded_walls needs resting walls")
+    pad = [1 if w else 0 for w in walled]
+    dims = [n + 2 * p for n, p in zip((nx, ny, nz), pad)]
+    solid = np.ones((dims[2], dims[1], dims[0]), np.uint8)
+    solid[pad[2]:pad[2] + nz, pad[1]:pad[1] + ny, pad[0]:pad[0] + nx] = 0
+    code = np.zeros_like(solid, dtype=np.int8)
+    size = (nx, ny, nz)
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                c = (x, y, z)
+                normals = []
+                for a in range(3):
+                    if not walled[a]:
+                        continue
+                    if c[a] == 0:
+                        normals.append(_axis_vec(a, 1))
+                    elif c[a] == size[a] - 1:
+                        normals.append(_axis_vec(a, -1))
+                if not normals:
+                    continue
+                if len(normals) == 1:
+                    k = plane_code(normals[0])
+                elif len(normals) == 2:
+                    k = concave_edge_code(*normals)
+                else:
+                    k = corner_code(np.sum(normals, axis=0))
+                code[z + pad[2], y + pad[1], x + pad[0]] = k
+    face_u = [None if not walled[i // 2] else ZERO for i in range(6)]
+    out = make_workload(wl.name + "_embedded", dims[0], dims[1], dims[2], wl.tau, face_u, wl.steps, wl.rho0,
+                        dict(wl.meta, pad=pad))
+    out.solid = solid
+    out.code = code
+    out.force = None if wl.force is None else np.array(wl.force, np.float64)
+    return out
+
+
+def pillar_channel(n=(24, 16, 12), axis: int = 2, flow: int = 0, block=((9, 14), (5, 10)), tau: float = 0.9,
+                   force: float = 2e-6) -> Workload:
+    """A rectangular pillar spanning a channel between two resting walls, driven by a
+    body force. ``axis`` is the pillar axis (its two faces are the walls), ``flow``
+    the force direction (perpendicular to ``axis``); the other two axes are periodic.
+    ``block`` gives the pillar's extent [lo, hi] (surface nodes included) on the two
+    axes other than ``axis``, in increasing axis order. The pillar's surface nodes are
+    boundary nodes with codes (planes, convex edges along the pillar, concave edges
+    and edge/plane junctions where it meets the walls); its interior is solid. ``n``
+    holds (n along axis, n along the first other axis, n along the second)."""
+    others = [a for a in range(3) if a != axis]
+    if flow not in others:
+        raise ValueError("the force must be perpendicular to the pillar")
+    dims = [0, 0, 0]
+    dims[axis] = n[2]
+    dims[others[0]] = n[0]
+    dims[others[1]] = n[1]
+    nx, ny, nz = dims
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    code = np.zeros((nz, ny, nx), np.int8)
+    (l0, h0), (l1, h1) = block
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                c = (x, y, z)
+                u, v, w = c[others[0]], c[others[1]], c[axis]
+                if not (l0 <= u <= h0 and l1 <= v <= h1):
+                    continue
+                if l0 < u < h0 and l1 < v < h1:
+                    solid[z, y, x] = 1
+                    continue
+                # surface node: bulk-side normals of the pillar faces it lies on
+                pn = []
+                if u == l0:
+                    pn.append(_axis_vec(others[0], -1))
+                if u == h0:
+                    pn.append(_axis_vec(others[0], 1))
+                if v == l1:
+                    pn.append(_axis_vec(others[1], -1))
+                if v == h1:
+                    pn.append(_axis_vec(others[1], 1))
+                wall = None
+                if w == 0:
+                    wall = _axis_vec(axis, 1)
+                elif w == dims[axis] - 1:
+                    wall = _axis_vec(axis, -1)
+                if len(pn) == 1:
+                    k = plane_code(pn[0]) if wall is None else concave_edge_code(pn[0], wall)
+                else:
+                    k = convex_edge_code(pn[0], pn[1]) if wall is None else junction_code(wall, pn[0], pn[1])
+                code[z, y, x] = k
+    face_u = [None] * 6
+    face_u[2 * axis] = ZERO
+    face_u[2 * axis + 1] = ZERO
+    wl = make_workload("pillar_channel", nx, ny, nz, tau, face_u,
+                       meta={"axis": axis, "flow": flow, "block": block, "force": force})
+    f = np.zeros(3)
+    f[flow] = force
+    wl.solid = solid
+    wl.code = code
+    wl.force = f
     return wl
 
 

@@ -41,10 +41,13 @@ def lib():
         L.orc_stream.argtypes = [C.c_int] * 3 + [_ip, _dp, _dp]
         L.orc_step.argtypes = [C.c_int] * 3 + [_ip, C.c_void_p, C.c_void_p, C.c_double, _dp, _dp, C.c_int]
         L.orc_run.argtypes = [C.c_int] * 3 + [_ip, C.c_void_p, C.c_void_p, C.c_double, C.c_int, _dp, _dp, C.c_int]
-        L.orc_step_geom.argtypes = [C.c_int] * 3 + [_ip, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, _dp, _dp,
-                                                    C.c_int]
-        L.orc_run_geom.argtypes = [C.c_int] * 3 + [_ip, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
-                                                   _dp, _dp, C.c_int]
+        L.orc_step_geom.argtypes = [C.c_int] * 3 + [_ip] + [C.c_void_p] * 5 + [C.c_double, _dp, _dp, C.c_int]
+        L.orc_run_geom.argtypes = [C.c_int] * 3 + [_ip] + [C.c_void_p] * 5 + [C.c_double, C.c_int, _dp, _dp,
+                                                                              C.c_int]
+        L.orc_collide_force.argtypes = [_dp, C.c_double, _dp]
+        L.orc_close_rule.argtypes = [C.c_int, _dp]
+        L.orc_rule_unknowns.argtypes = [C.c_int, _ip]
+        L.orc_check_geometry.argtypes = [C.c_int] * 3 + [_ip, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]
         L.orc_init_equilibrium.argtypes = [C.c_int] * 3 + [C.c_double, _dp]
         L.orc_macros.argtypes = [C.c_int] * 3 + [_dp, _dp, _dp]
         L.orc_reduce.argtypes = [C.c_int] * 3 + [_dp, C.c_void_p, _dp]
@@ -54,7 +57,8 @@ def lib():
         L.orc_lattice.argtypes = [_ip, _dp, _ip]
         L.orc_threads.restype = C.c_int
         for name in ("orc_close_face", "orc_close_edge", "orc_close_corner", "orc_close_face_pressure", "orc_stream",
-                     "orc_step", "orc_run", "orc_step_geom", "orc_run_geom", "orc_sources", "orc_update_gathered"):
+                     "orc_step", "orc_run", "orc_step_geom", "orc_run_geom", "orc_sources", "orc_update_gathered",
+                     "orc_close_rule", "orc_rule_unknowns", "orc_check_geometry"):
             getattr(L, name).restype = C.c_int
         _LIB = L
     return _LIB
@@ -111,6 +115,35 @@ def close_face_pressure(face: int, f, rho0: float, u_t, form: int = 0):
     return g, vn.value
 
 
+def collide_force(f, tau: float, force) -> np.ndarray:
+    """BGK collision with the body force of eq. gravity (velocity shift tau F / rho)."""
+    g = np.array(f, np.float64)
+    lib().orc_collide_force(g, float(tau), np.ascontiguousarray(force, np.float64))
+    return g
+
+
+def close_rule(code: int, f) -> np.ndarray:
+    """Boundary rule of a node code of a general geometry (no-slip)."""
+    g = np.array(f, np.float64)
+    _check(lib().orc_close_rule(int(code), g), "close_rule")
+    return g
+
+
+def rule_unknowns(code: int) -> np.ndarray:
+    """Boolean mask of the populations the rule of ``code`` overwrites."""
+    out = np.zeros(Q, np.int32)
+    _check(lib().orc_rule_unknowns(int(code), out), "rule_unknowns")
+    return out.astype(bool)
+
+
+def check_geometry(lat: "Lattice") -> int:
+    """-1 if the lattice's node codes are consistent with its solid nodes and walls,
+    else the flat index of the first offending node."""
+    bad = C.c_int64(0)
+    rc = lib().orc_check_geometry(*lat.dims(), lat.kinds, lat._solid_ptr, lat._code_ptr, C.byref(bad))
+    return -1 if rc == 0 else int(bad.value) - 1
+
+
 def close_edge(face_a: int, face_b: int, f, rho_p: float = -1.0) -> np.ndarray:
     """No-slip edge; rho_p > 0 when the edge borders a pressure plane of that density."""
     g = np.array(f, np.float64)
@@ -133,9 +166,11 @@ class Lattice:
     prescribed velocity; for a pressure face its tangential part), or None for a
     periodic face. ``ptabs[i]`` is the (n2, n1) prescribed density of a pressure face.
     ``solid`` is an optional (nz, ny, nx) mask of solid nodes (mid-grid bounce-back).
+    ``code`` is an optional (nz, ny, nx) int8 array of on-site boundary rules (see
+    ``close_rule``); ``force`` the body force of eq. gravity.
     """
 
-    def __init__(self, nx, ny, nz, kinds, utabs, tau, ptabs=None, solid=None):
+    def __init__(self, nx, ny, nz, kinds, utabs, tau, ptabs=None, solid=None, code=None, force=None):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.kinds = np.ascontiguousarray(kinds, np.int32)
         self.tau = float(tau)
@@ -159,15 +194,27 @@ class Lattice:
         self.solid = None if solid is None else np.ascontiguousarray(solid, np.uint8)
         if self.solid is not None and self.solid.shape != (self.nz, self.ny, self.nx):
             raise ValueError("solid mask must be (nz, ny, nx)")
+        self.code = None if code is None else np.ascontiguousarray(code, np.int8)
+        if self.code is not None and self.code.shape != (self.nz, self.ny, self.nx):
+            raise ValueError("code array must be (nz, ny, nx)")
+        self.force = None if force is None else np.ascontiguousarray(force, np.float64).reshape(3)
 
     @property
     def _solid_ptr(self):
         return None if self.solid is None else self.solid.ctypes.data
 
+    @property
+    def _code_ptr(self):
+        return None if self.code is None else self.code.ctypes.data
+
+    @property
+    def _force_ptr(self):
+        return None if self.force is None else self.force.ctypes.data
+
     @classmethod
     def from_workload(cls, wl):
         return cls(wl.nx, wl.ny, wl.nz, wl.kinds, wl.utabs, wl.tau, getattr(wl, "ptabs", None),
-                   getattr(wl, "solid", None))
+                   getattr(wl, "solid", None), getattr(wl, "code", None), getattr(wl, "force", None))
 
     @property
     def shape(self):
@@ -202,16 +249,16 @@ FORM_EXPLICIT, FORM_COMPACT, FORM_COMPACT_NO_N = 0, 1, 3
 def step(lat: Lattice, f, form: int = 0) -> np.ndarray:
     fin = np.ascontiguousarray(f, np.float64)
     out = np.zeros(lat.shape)
-    _check(lib().orc_step_geom(*lat.dims(), lat.kinds, lat._ptrs, lat._pptrs, lat._solid_ptr, lat.tau, fin, out,
-                               form), "step")
+    _check(lib().orc_step_geom(*lat.dims(), lat.kinds, lat._ptrs, lat._pptrs, lat._solid_ptr, lat._code_ptr,
+                               lat._force_ptr, lat.tau, fin, out, form), "step")
     return out
 
 
 def run(lat: Lattice, f, nsteps: int, form: int = 0) -> np.ndarray:
     g = np.array(f, np.float64, order="C")
     work = np.empty_like(g)
-    _check(lib().orc_run_geom(*lat.dims(), lat.kinds, lat._ptrs, lat._pptrs, lat._solid_ptr, lat.tau, int(nsteps),
-                              g, work, form), "run")
+    _check(lib().orc_run_geom(*lat.dims(), lat.kinds, lat._ptrs, lat._pptrs, lat._solid_ptr, lat._code_ptr,
+                              lat._force_ptr, lat.tau, int(nsteps), g, work, form), "run")
     return g
 
 

@@ -47,6 +47,18 @@
  *   R8 pressure planes: edges and corners next to one take the buried-link values
  *      that make their density the prescribed one (eq. buried_rho, corner variant);
  *      the along-edge momentum correction is the same as for velocity planes.
+ *   R9 convex edges (eq. edge2): after bounce-back of the population whose source is
+ *      solid, N_i is subtracted from every population travelling into the bulk
+ *      (c_i.d > 0, d the edge's bulk normal); the four of them with c_i.e != 0 carry
+ *      the whole along-edge momentum away.
+ *   R10 edge/plane junctions: the rest population is printed as 12/36 of the sum of
+ *      the 18 moving populations, which at rest would remove a ninth of the node's
+ *      density every step; it is read as 12/36 of the node density, i.e. one half of
+ *      the sum of the moving populations. Only convex edges meet a plane this way: a
+ *      concave edge ending on a perpendicular plane is a corner (eq. corner).
+ *   R11 body force (eq. gravity): the equilibrium of the collision takes the velocity
+ *      u + tau F / rho; the reported velocity is that of the stored post-collision
+ *      state, u + F / rho.
  */
 #include <math.h>
 #include <stdint.h>
@@ -122,6 +134,16 @@ void orc_collide(double* f, double tau) {
   double m[4], feq[Q];
   orc_moments(f, m);
   orc_feq(m[0], m + 1, feq);
+  for (int k = 0; k < Q; ++k) f[k] = f[k] - (f[k] - feq[k]) / tau;
+}
+
+/* BGK collision under a body force F (eq. gravity, reading R11): the equilibrium
+ * takes the velocity v + tau F / rho. */
+void orc_collide_force(double* f, double tau, const double* force) {
+  double m[4], feq[Q], v[3];
+  orc_moments(f, m);
+  for (int a = 0; a < 3; ++a) v[a] = m[a + 1] + tau * force[a] / m[0];
+  orc_feq(m[0], v, feq);
   for (int k = 0; k < Q; ++k) f[k] = f[k] - (f[k] - feq[k]) / tau;
 }
 
@@ -423,6 +445,141 @@ int orc_close_corner(int face_x, int face_y, int face_z, double* f, double rho_p
 }
 
 /* ----------------------------------------------------------------------------------
+ * Boundary nodes of a general geometry (Sec. "On-site no-slip boundary condition",
+ * complex geometries): the normal is stored on the node as an integer code.
+ *   1..6      plane, inward normal c_code (eq. bbshort with v = 0)
+ *   7..18     concave edge whose bulk normal is the diagonal c_code (eq. edge)
+ *   -18..-7   convex edge whose bulk normal is the diagonal c_-code (eq. edge2)
+ *   19..26    corner with bulk normal (sx, sy, sz), code = 19 + [sx<0] + 2[sy<0] + 4[sz<0]
+ *             (eq. corner)
+ *   27..50    junction of a convex edge with the plane perpendicular to it:
+ *             code = 27 + 4 (p - 1) + j, plane normal c_p (p = 1..6), edge bulk normal
+ *             the j-th (j = 0..3, increasing index) diagonal c_i with c_i.c_p = 0
+ * -------------------------------------------------------------------------------- */
+enum { RULE_NONE = 0, RULE_PLANE, RULE_CONCAVE, RULE_CONVEX, RULE_CORNER, RULE_JUNCTION };
+
+typedef struct {
+  int type;
+  int n[3]; /* plane: normal; edges: first plane normal; corner: (sx, sy, sz); junction: plane normal */
+  int m[3]; /* edges: second plane normal */
+  int d[3]; /* edges and junction: bulk normal of the edge */
+} rule_t;
+
+/* Split a diagonal lattice vector into its two axis components. */
+static void split_diagonal(const int d[3], int a[3], int b[3]) {
+  int first = 1;
+  for (int i = 0; i < 3; ++i) a[i] = b[i] = 0;
+  for (int i = 0; i < 3; ++i) {
+    if (d[i] == 0) continue;
+    if (first) { a[i] = d[i]; first = 0; }
+    else b[i] = d[i];
+  }
+}
+
+static int decode_rule(int code, rule_t* r) {
+  memset(r, 0, sizeof(*r));
+  int ac = code < 0 ? -code : code;
+  if (code >= 1 && code <= 6) {
+    r->type = RULE_PLANE;
+    for (int i = 0; i < 3; ++i) r->n[i] = CV[code - 1][i];
+  } else if (ac >= 7 && ac <= 18) {
+    r->type = code > 0 ? RULE_CONCAVE : RULE_CONVEX;
+    for (int i = 0; i < 3; ++i) r->d[i] = CV[ac - 1][i];
+    split_diagonal(r->d, r->n, r->m);
+  } else if (code >= 19 && code <= 26) {
+    int b = code - 19;
+    r->type = RULE_CORNER;
+    r->n[0] = (b & 1) ? -1 : 1;
+    r->n[1] = (b & 2) ? -1 : 1;
+    r->n[2] = (b & 4) ? -1 : 1;
+  } else if (code >= 27 && code <= 50) {
+    int p = (code - 27) / 4, j = (code - 27) % 4, seen = 0;
+    r->type = RULE_JUNCTION;
+    for (int i = 0; i < 3; ++i) r->n[i] = CV[p][i];
+    for (int k = 6; k < 18; ++k) {
+      if (dot_ci(k, r->n) != 0) continue;
+      if (seen++ == j) {
+        for (int i = 0; i < 3; ++i) r->d[i] = CV[k][i];
+        break;
+      }
+    }
+  } else {
+    return ORC_ERR_ARG;
+  }
+  return ORC_OK;
+}
+
+static int same_vector(int k, const int v[3]) { return CV[k][0] == v[0] && CV[k][1] == v[1] && CV[k][2] == v[2]; }
+
+/* Populations the rule overwrites (its unknowns). */
+static int rule_unknown(const rule_t* r, int k) {
+  switch (r->type) {
+    case RULE_PLANE: return dot_ci(k, r->n) > 0;
+    case RULE_CONCAVE: return dot_ci(k, r->n) > 0 || dot_ci(k, r->m) > 0;
+    case RULE_CONVEX: return same_vector(k, r->d);
+    case RULE_CORNER:
+      return CV[k][0] * r->n[0] > 0 || CV[k][1] * r->n[1] > 0 || CV[k][2] * r->n[2] > 0;
+    case RULE_JUNCTION: return dot_ci(k, r->n) > 0 || same_vector(k, r->d);
+    default: return 0;
+  }
+}
+
+/* Convex edge (eq. edge2, reading R9): the population coming from the solid side is
+ * bounced back; then N_i = 1/4 (c_i.e) sum_j f_j (c_j.e), e = n1 x n2, is subtracted
+ * from every population travelling into the bulk (c_i.d > 0). */
+static void close_convex_edge(double* f, const rule_t* r) {
+  int e[3] = {r->n[1] * r->m[2] - r->n[2] * r->m[1], r->n[2] * r->m[0] - r->n[0] * r->m[2],
+              r->n[0] * r->m[1] - r->n[1] * r->m[0]};
+  for (int k = 0; k < Q; ++k)
+    if (same_vector(k, r->d)) f[k] = f[opposite(k)];
+  double P = 0.0;
+  for (int j = 0; j < Q; ++j) P += f[j] * dot_ci(j, e);
+  for (int k = 0; k < Q; ++k)
+    if (dot_ci(k, r->d) > 0) f[k] -= 0.25 * dot_ci(k, e) * P;
+}
+
+/* Junction of a convex edge with a perpendicular plane (reading R10): bounce-back of
+ * the populations coming from outside (through the plane or from the edge's solid
+ * side), rest population = 12/36 of the node density. */
+static void close_junction(double* f, const rule_t* r) {
+  for (int k = 0; k < Q; ++k)
+    if (rule_unknown(r, k)) f[k] = f[opposite(k)];
+  double s = 0.0;
+  for (int k = 0; k < Q - 1; ++k) s += f[k];
+  F(19) = 0.5 * s;
+}
+
+/* Applies the rule of a node code (all velocities zero: no-slip walls). */
+static int close_rule(int code, double* f, int form) {
+  rule_t r;
+  if (decode_rule(code, &r)) return ORC_ERR_ARG;
+  static const double zero[3] = {0.0, 0.0, 0.0};
+  switch (r.type) {
+    case RULE_PLANE: close_face_form(code - 1, form, f, zero, -1.0); break;
+    case RULE_CONCAVE: close_edge_normals(f, r.n, r.m, -1.0); break;
+    case RULE_CONVEX: close_convex_edge(f, &r); break;
+    case RULE_CORNER: {
+      int n1[3] = {r.n[0], 0, 0}, n2[3] = {0, r.n[1], 0}, n3[3] = {0, 0, r.n[2]};
+      close_corner_normals(f, n1, n2, n3, -1.0);
+      break;
+    }
+    case RULE_JUNCTION: close_junction(f, &r); break;
+    default: return ORC_ERR_ARG;
+  }
+  return ORC_OK;
+}
+
+int orc_close_rule(int code, double* f) { return close_rule(code, f, 0); }
+
+/* unknown[k] = 1 where the rule of `code` overwrites population k. */
+int orc_rule_unknowns(int code, int* unknown) {
+  rule_t r;
+  if (decode_rule(code, &r)) return ORC_ERR_ARG;
+  for (int k = 0; k < Q; ++k) unknown[k] = rule_unknown(&r, k);
+  return ORC_OK;
+}
+
+/* ----------------------------------------------------------------------------------
  * Lattice: streaming, classification, one time step.
  * -------------------------------------------------------------------------------- */
 typedef struct {
@@ -432,6 +589,9 @@ typedef struct {
                              tangential velocity; the normal component is ignored) */
   const double* ptab[6];  /* [n2][n1] prescribed density per pressure face */
   const unsigned char* solid; /* optional [nz][ny][nx]: nonzero marks a solid node */
+  const signed char* code;    /* optional [nz][ny][nx]: boundary rule of the node (0: none) */
+  double force[3];            /* body force (eq. gravity) */
+  int forced;                 /* force != 0 */
   double tau;
 } lattice_t;
 
@@ -483,6 +643,15 @@ static int64_t face_index(const lattice_t* L, int face, int x, int y, int z) {
  * (NaN marks an unknown population). */
 static int update_node(const lattice_t* L, int x, int y, int z, double* f, int form) {
   int c[3] = {x, y, z};
+  int code = L->code ? L->code[((int64_t)z * L->ny + y) * L->nx + x] : 0;
+  if (code != 0) {
+    if (close_rule(code, f, form)) return ORC_ERR_ARG;
+    for (int k = 0; k < Q; ++k)
+      if (isnan(f[k])) return ORC_ERR_UNFILLED;
+    if (L->forced) orc_collide_force(f, L->tau, L->force);
+    else orc_collide(f, L->tau);
+    return ORC_OK;
+  }
   int faces[3], nf = 0;
   double rho_p = -1.0; /* density of a bordering pressure plane, if any */
   for (int a = 0; a < 3; ++a) {
@@ -512,7 +681,8 @@ static int update_node(const lattice_t* L, int x, int y, int z, double* f, int f
   }
   for (int k = 0; k < Q; ++k)
     if (isnan(f[k])) return ORC_ERR_UNFILLED;
-  orc_collide(f, L->tau);
+  if (L->forced) orc_collide_force(f, L->tau, L->force);
+  else orc_collide(f, L->tau);
   return ORC_OK;
 }
 
@@ -520,6 +690,9 @@ static int make_lattice(lattice_t* L, int nx, int ny, int nz, const int* kind, c
                         const double* const* ptab, double tau) {
   L->nx = nx; L->ny = ny; L->nz = nz; L->tau = tau;
   L->solid = NULL;
+  L->code = NULL;
+  L->force[0] = L->force[1] = L->force[2] = 0.0;
+  L->forced = 0;
   for (int i = 0; i < 6; ++i) {
     L->kind[i] = kind[i];
     L->utab[i] = utab ? utab[i] : NULL;
@@ -538,8 +711,51 @@ static int64_t gather_source(const lattice_t* L, int x, int y, int z, int k) {
   int64_t node = ((int64_t)z * L->ny + y) * L->nx + x;
   int64_t s = pull_source(L, x, y, z, k);
   if (s < 0) return -1;
-  if (L->solid && L->solid[s]) return (int64_t)opposite(k) * N + node;
+  if (L->solid && L->solid[s]) {
+    /* a node with an on-site rule overwrites this population (checked beforehand) */
+    if (L->code && L->code[node] != 0) return -1;
+    return (int64_t)opposite(k) * N + node;
+  }
   return (int64_t)k * N + s;
+}
+
+/* Geometry check: a node with a rule is fluid, its code is valid, and every population
+ * it cannot stream (source solid or outside a walled axis) is one the rule overwrites.
+ * Returns the first offending node + 1 in *bad (0 if none). */
+static int geometry_check(const lattice_t* L, int64_t* bad) {
+  *bad = 0;
+  if (!L->code) return ORC_OK;
+  for (int z = 0; z < L->nz; ++z)
+    for (int y = 0; y < L->ny; ++y)
+      for (int x = 0; x < L->nx; ++x) {
+        int64_t node = ((int64_t)z * L->ny + y) * L->nx + x;
+        int code = L->code[node];
+        if (code == 0) continue;
+        rule_t r;
+        int ok = !decode_rule(code, &r) && !(L->solid && L->solid[node]);
+        for (int k = 0; ok && k < Q; ++k) {
+          int64_t s = pull_source(L, x, y, z, k);
+          int blocked = s < 0 || (L->solid && L->solid[s]);
+          if (blocked && !rule_unknown(&r, k)) ok = 0;
+        }
+        if (!ok) {
+          *bad = node + 1;
+          return ORC_ERR_ARG;
+        }
+      }
+  return ORC_OK;
+}
+
+int orc_check_geometry(int nx, int ny, int nz, const int* kind, const unsigned char* solid, const signed char* code,
+                       int64_t* bad) {
+  lattice_t L;
+  double dummy = 0.0;
+  const double* none[6] = {&dummy, &dummy, &dummy, &dummy, &dummy, &dummy};
+  int rc = make_lattice(&L, nx, ny, nz, kind, none, none, 1.0);
+  if (rc) return rc;
+  L.solid = solid;
+  L.code = code;
+  return geometry_check(&L, bad);
 }
 
 /* Pull streaming only: out[k][node] = in[k][node - c_k], NaN where unknown. */
@@ -566,11 +782,20 @@ int orc_stream(int nx, int ny, int nz, const int* kind, const double* fin, doubl
 /* One time step fin -> fout (streaming, closure, collision). Solid nodes (when a mask
  * is given) keep their populations unchanged. */
 int orc_step_geom(int nx, int ny, int nz, const int* kind, const double* const* utab, const double* const* ptab,
-                  const unsigned char* solid, double tau, const double* fin, double* fout, int form) {
+                  const unsigned char* solid, const signed char* code, const double* force, double tau,
+                  const double* fin, double* fout, int form) {
   lattice_t L;
   int rc = make_lattice(&L, nx, ny, nz, kind, utab, ptab, tau);
   if (rc) return rc;
   L.solid = solid;
+  L.code = code;
+  if (force) {
+    for (int a = 0; a < 3; ++a) L.force[a] = force[a];
+    L.forced = force[0] != 0.0 || force[1] != 0.0 || force[2] != 0.0;
+  }
+  int64_t bad;
+  rc = geometry_check(&L, &bad);
+  if (rc) return rc;
   int64_t N = (int64_t)nx * ny * nz;
   int err = 0;
 #pragma omp parallel for schedule(static) reduction(| : err)
@@ -596,17 +821,18 @@ int orc_step_geom(int nx, int ny, int nz, const int* kind, const double* const* 
 
 int orc_step(int nx, int ny, int nz, const int* kind, const double* const* utab, const double* const* ptab,
              double tau, const double* fin, double* fout, int form) {
-  return orc_step_geom(nx, ny, nz, kind, utab, ptab, NULL, tau, fin, fout, form);
+  return orc_step_geom(nx, ny, nz, kind, utab, ptab, NULL, NULL, NULL, tau, fin, fout, form);
 }
 
 /* nsteps time steps; f holds the initial and the final state, work is scratch of the
  * same size. */
 int orc_run_geom(int nx, int ny, int nz, const int* kind, const double* const* utab, const double* const* ptab,
-                 const unsigned char* solid, double tau, int nsteps, double* f, double* work, int form) {
+                 const unsigned char* solid, const signed char* code, const double* force, double tau, int nsteps,
+                 double* f, double* work, int form) {
   int64_t n = (int64_t)Q * nx * ny * nz;
   double *a = f, *b = work;
   for (int s = 0; s < nsteps; ++s) {
-    int rc = orc_step_geom(nx, ny, nz, kind, utab, ptab, solid, tau, a, b, form);
+    int rc = orc_step_geom(nx, ny, nz, kind, utab, ptab, solid, code, force, tau, a, b, form);
     if (rc) return rc;
     double* t = a; a = b; b = t;
   }
@@ -616,7 +842,7 @@ int orc_run_geom(int nx, int ny, int nz, const int* kind, const double* const* u
 
 int orc_run(int nx, int ny, int nz, const int* kind, const double* const* utab, const double* const* ptab,
             double tau, int nsteps, double* f, double* work, int form) {
-  return orc_run_geom(nx, ny, nz, kind, utab, ptab, NULL, tau, nsteps, f, work, form);
+  return orc_run_geom(nx, ny, nz, kind, utab, ptab, NULL, NULL, NULL, tau, nsteps, f, work, form);
 }
 
 /* f = f_eq(rho0, 0) on every node (the initial, post-collision state). */
