@@ -177,6 +177,44 @@ LBM_API lbm_status lbm_get_populations(lbm_ctx* ctx, void* dst, int z0, int nzs,
  * A/B scheme only (LBM_ERR_ARG for AA). Synchronises. */
 LBM_API lbm_status lbm_set_solid(lbm_ctx* ctx, const uint8_t* solid);
 
+/* General geometry (Sec. "On-site no-slip boundary condition", complex geometries):
+ * `solid` (as for lbm_set_solid, may be NULL) and `code`, a HOST array [nz][ny][nx]
+ * of int8 (may be NULL; both copied, not retained) naming the on-site rule of each
+ * boundary node by its normal, written as the paper's lattice-vector index i of c_i
+ * (the normal points into the fluid; every such wall is at rest):
+ *     0          no rule: a bulk node, a face/edge/corner of the box (classified from
+ *                the face specs as usual), or a node taking mid-grid bounce-back from
+ *                its solid neighbours;
+ *     1..6       plane with normal c_i: eq. bbshort with v = 0 (density from the plane's
+ *                relation);
+ *     7..18      concave edge whose bulk normal is the diagonal c_i = n1 + n2: eq. edge
+ *                (bounce-back, along-edge correction, buried links eq. buried);
+ *     -7..-18    convex edge with bulk normal c_-code: the population from the solid
+ *                side is bounced back, then 1/4 (c_i.e) sum_j f_j (c_j.e) (eq. edge2,
+ *                e = n1 x n2) is subtracted from every population with c_i.c_-code > 0;
+ *     19..26     corner with normal (sx, sy, sz): code 19 + [sx<0] + 2[sy<0] + 4[sz<0];
+ *                eq. corner;
+ *     27..50     a convex edge meeting the plane perpendicular to it: code
+ *                27 + 4 (p - 1) + j for the plane normal c_p (p = 1..6) and the edge's
+ *                bulk normal the j-th (j = 0..3, increasing index) diagonal c_i with
+ *                c_i.c_p = 0. The populations coming through the plane or from the edge's
+ *                solid side are bounced back and the rest population is set to 12/36 of
+ *                the node density (the printed factor taken as a share of the density,
+ *                which keeps a resting node at rest).
+ * A node with a code must be fluid, and every population it cannot stream (source solid,
+ * or outside a walled axis) must be one its rule sets; otherwise LBM_ERR_ARG names the
+ * node. Extra traffic: 4 bytes per node per step. A/B scheme only; not while the context
+ * is attached to a batch (LBM_ERR_STATE). Synchronises. */
+LBM_API lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* solid, const int8_t* code);
+
+/* Uniform body force F (force per volume, lattice units) acting on every fluid node
+ * (Sec. "Numerical Results", eq. gravity): the collision relaxes toward the equilibrium
+ * at the velocity u + tau F / rho and so adds F to each node's momentum per step. The
+ * velocity reported by lbm_macros and the residual is that of the stored post-collision
+ * state, u + F / rho. F = 0 switches the force off. Not finite: LBM_ERR_ARG. A/B scheme
+ * only; not while attached to a batch (LBM_ERR_STATE). Takes effect with the next step. */
+LBM_API lbm_status lbm_set_body_force(lbm_ctx* ctx, const double force[3]);
+
 /* Block the host until the context's stream is idle; reports asynchronous errors. */
 LBM_API lbm_status lbm_sync(lbm_ctx* ctx);
 

@@ -40,6 +40,8 @@ EXPORTS = {
     "lbm_get_populations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "lbm_sync": (C.c_int, [C.c_void_p]),
     "lbm_set_solid": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lbm_set_geometry": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_set_body_force": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "lbm_info": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_batch_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
@@ -236,10 +238,28 @@ class Lattice:
             raise ValueError(f"solid mask shape {m.shape} != {(self.nz, self.ny, self.nx)}")
         check(lib().lbm_set_solid(self.ctx, C.c_void_p(m.ctypes.data)), self.ctx)
 
+    def set_geometry(self, solid=None, code=None):
+        """General geometry: solid nodes (uint8, nonzero = solid) and on-site rule codes
+        (int8, the normal as a lattice-vector index; see lbm_set_geometry), both
+        (nz, ny, nx) or None; A/B scheme only."""
+        shape = (self.nz, self.ny, self.nx)
+        m = None if solid is None else np.ascontiguousarray(solid, np.uint8)
+        c = None if code is None else np.ascontiguousarray(code, np.int8)
+        for name, a in (("solid", m), ("code", c)):
+            if a is not None and a.shape != shape:
+                raise ValueError(f"{name} shape {a.shape} != {shape}")
+        check(lib().lbm_set_geometry(self.ctx, None if m is None else C.c_void_p(m.ctypes.data),
+                                     None if c is None else C.c_void_p(c.ctypes.data)), self.ctx)
+
+    def set_body_force(self, force):
+        """Uniform body force F (eq. gravity); A/B scheme only."""
+        f = (C.c_double * 3)(*[float(v) for v in force])
+        check(lib().lbm_set_body_force(self.ctx, f), self.ctx)
+
     @classmethod
     def from_workload(cls, wl, precision="f32", **kw):
         """A lattice for any object with nx, ny, nz, tau, rho0, kinds, utabs (and ptabs
-        for pressure faces, solid for solid nodes)."""
+        for pressure faces, solid / code for a geometry, force for a body force)."""
         ptabs = getattr(wl, "ptabs", None) or [None] * 6
         faces = []
         for k, t, p in zip(wl.kinds, wl.utabs, ptabs):
@@ -250,8 +270,13 @@ class Lattice:
             else:
                 faces.append(t)
         lat = cls(wl.nx, wl.ny, wl.nz, wl.tau, faces, precision, wl.rho0, **kw)
-        if getattr(wl, "solid", None) is not None:
-            lat.set_solid(wl.solid)
+        solid, code = getattr(wl, "solid", None), getattr(wl, "code", None)
+        if code is not None:
+            lat.set_geometry(solid, code)
+        elif solid is not None:
+            lat.set_solid(solid)
+        if getattr(wl, "force", None) is not None:
+            lat.set_body_force(wl.force)
         return lat
 
     # -- lifetime -------------------------------------------------------------------

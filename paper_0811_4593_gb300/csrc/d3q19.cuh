@@ -37,4 +37,20 @@ __host__ __device__ constexpr int w36(int k) { return k < 6 ? 2 : (k < 18 ? 1 : 
 template <typename T>
 __host__ __device__ constexpr T wgt(int k) { return T(w36(k)) / T(36); }
 
+// Axis (0, 1, 2) and sign of the axis vector c_k (k < 6).
+__host__ __device__ constexpr int axis_of(int k) { return cx(k) != 0 ? 0 : (cy(k) != 0 ? 1 : 2); }
+__host__ __device__ constexpr int sign_of(int k) { return cx(k) + cy(k) + cz(k); }
+
+// The diagonal with index j (0..3, in increasing population index) among the twelve
+// diagonals perpendicular to the axis vector c_p: the bulk normal of junction codes.
+__host__ __device__ constexpr int junction_diagonal(int p, int j) {
+  int seen = 0, r = -1;
+  for (int k = 6; k < 18; ++k)
+    if (cx(k) * cx(p) + cy(k) * cy(p) + cz(k) * cz(p) == 0) {
+      if (seen == j) r = k;
+      ++seen;
+    }
+  return r;
+}
+
 }  // namespace lbm

@@ -366,6 +366,102 @@ __device__ __forceinline__ void apply_boundary(int code, const SweepArgs& a, uin
   }
 }
 
+// ---------------------------------------------------------------------------------
+// On-site rules of a general geometry (Sec. "On-site no-slip boundary condition",
+// complex geometries): every wall is at rest.
+// ---------------------------------------------------------------------------------
+
+// Convex edge with bulk normal d = (DX, DY, DZ) (a diagonal: the sum of the two plane
+// normals) and edge direction e = n1 x n2 (eq. edge2): the population coming from the
+// solid side, c = d, is bounced back; then 1/4 (c_i.e) sum_j h_j (c_j.e) is subtracted
+// from every population travelling into the bulk (c_i.d > 0), which removes all
+// momentum along the edge (four of them have c_i.e = +-1).
+template <int DX, int DY, int DZ>
+struct ConvexRule {
+  static constexpr int n1x = DX != 0 ? DX : 0, n1y = DX == 0 ? DY : 0, n1z = 0;
+  static constexpr int n2x = 0, n2y = DX != 0 ? DY : 0, n2z = DZ;
+  static constexpr int ex = n1y * n2z - n1z * n2y, ey = n1z * n2x - n1x * n2z, ez = n1x * n2y - n1y * n2x;
+  static constexpr int KD = vel_index(DX, DY, DZ);
+  __host__ __device__ static constexpr int along(int k) { return cx(k) * ex + cy(k) * ey + cz(k) * ez; }
+  __host__ __device__ static constexpr int into_bulk(int k) { return cx(k) * DX + cy(k) * DY + cz(k) * DZ > 0; }
+};
+
+template <int DX, int DY, int DZ, typename T>
+__device__ __forceinline__ void close_convex(T (&h)[Q]) {
+  using R = ConvexRule<DX, DY, DZ>;
+  static_assert(R::KD >= 0 && R::ex * R::ex + R::ey * R::ey + R::ez * R::ez == 1, "diagonal bulk normal");
+  h[R::KD] = h[opp(R::KD)];
+  T P = T(0);
+  static_for<0, Q>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    if constexpr (R::along(k) != 0) P += T(R::along(k)) * h[k];
+  });
+  const T q = T(0.25) * P;
+  static_for<0, Q>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    if constexpr (R::into_bulk(k) && R::along(k) != 0) h[k] -= T(R::along(k)) * q;
+  });
+}
+
+// Convex edge with bulk normal d = (DX, DY, DZ) meeting the plane with inward normal
+// SG e_A: bounce-back of the populations coming through the plane (SG c_A > 0) or from
+// the edge's solid side (c = d); rest population = 12/36 of the node density, i.e. one
+// half of the moving populations (the sum of shifted populations obeys the same
+// relation, since the weights of the moving populations add up to 24/36).
+template <int A, int SG, int DX, int DY, int DZ, typename T>
+__device__ __forceinline__ void close_junction(T (&h)[Q]) {
+  constexpr int KD = vel_index(DX, DY, DZ);
+  static_assert(KD >= 0, "diagonal bulk normal");
+  static_for<0, Q>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    if constexpr (SG * ca(k, A) > 0 || k == KD) h[k] = h[opp(k)];
+  });
+  T s = T(0);
+  static_for<0, Q - 1>([&](auto kc) { s += h[decltype(kc)::value]; });
+  h[Q - 1] = T(0.5) * s;
+}
+
+
+// Rule R of the geometry word (see SOLID_NODE): R = 1..6 planes c_R, 7..18 concave
+// edges with bulk normal c_R, 19..26 corners, 27..50 junctions, 51..62 convex edges
+// with bulk normal c_(R-44).
+template <int R, typename T>
+__device__ __forceinline__ void rule_case(T (&h)[Q], double ref) {
+  if constexpr (R >= 1 && R <= 6) {
+    constexpr int k = R - 1;
+    const FaceVals<T> rest = {{T(0), T(0), T(0)}, 1.0};
+    close_face<axis_of(k), sign_of(k)>(h, rest, ref);
+  } else if constexpr (R >= 7 && R <= 18) {
+    constexpr int k = R - 1;
+    constexpr int A1 = cx(k) != 0 ? 0 : 1;
+    constexpr int S1 = A1 == 0 ? cx(k) : cy(k);
+    constexpr int A2 = cz(k) != 0 ? 2 : 1;
+    constexpr int S2 = A2 == 2 ? cz(k) : cy(k);
+    close_edge<A1, S1, A2, S2>(h, false, T(0));
+  } else if constexpr (R >= 19 && R <= 26) {
+    constexpr int b = R - 19;
+    close_corner<(b & 1) ? -1 : 1, (b & 2) ? -1 : 1, (b & 4) ? -1 : 1>(h, false, T(0));
+  } else if constexpr (R >= 27 && R <= 50) {
+    constexpr int p = (R - 27) / 4;
+    constexpr int d = junction_diagonal(p, (R - 27) % 4);
+    close_junction<axis_of(p), sign_of(p), cx(d), cy(d), cz(d)>(h);
+  } else if constexpr (R >= 51 && R <= 62) {
+    constexpr int k = R - 45;
+    close_convex<cx(k), cy(k), cz(k)>(h);
+  }
+}
+
+template <int LO, int HI, typename T>
+__device__ __forceinline__ void apply_rule(uint32_t r, T (&h)[Q], double ref) {
+  if constexpr (LO == HI) {
+    rule_case<LO>(h, ref);
+  } else {
+    constexpr int MID = (LO + HI) / 2;
+    if (r <= uint32_t(MID)) apply_rule<LO, MID>(r, h, ref);
+    else apply_rule<MID + 1, HI>(r, h, ref);
+  }
+}
+
 // Density deviation, velocity, and BGK relaxation toward the second-order
 // equilibrium (eq. rho, eq. vel, eq. feq, eq. bgk) on shifted populations:
 //   h_i^eq = w_i (drho + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u^2)).
@@ -434,6 +530,12 @@ template <> __device__ __forceinline__ float rho0_of<float>(const SweepArgs& a) 
 template <typename T> __device__ __forceinline__ T omega_of(const SweepArgs& a);
 template <> __device__ __forceinline__ double omega_of<double>(const SweepArgs& a) { return a.omega; }
 template <> __device__ __forceinline__ float omega_of<float>(const SweepArgs& a) { return a.omegaf; }
+template <typename T> __device__ __forceinline__ T force_of(const SweepArgs& a, int i);
+template <> __device__ __forceinline__ double force_of<double>(const SweepArgs& a, int i) { return a.force[i]; }
+template <> __device__ __forceinline__ float force_of<float>(const SweepArgs& a, int i) { return a.forcef[i]; }
+template <typename T> __device__ __forceinline__ T tforce_of(const SweepArgs& a, int i);
+template <> __device__ __forceinline__ double tforce_of<double>(const SweepArgs& a, int i) { return a.tforce[i]; }
+template <> __device__ __forceinline__ float tforce_of<float>(const SweepArgs& a, int i) { return a.tforcef[i]; }
 
 // Deterministic block sum of four doubles; thread 0 of the block gets the totals.
 __device__ __forceinline__ void block_sum4(double (&v)[4], double* out) {
@@ -491,7 +593,9 @@ enum StreamMode : int { STREAM_AB = 0, STREAM_AA_GATHER = 1, STREAM_AA_LOCAL = 2
 // node x (the "swapped" state); after the gather step the array holds the streamed
 // populations in natural slots, after the local step the swapped post-collision state
 // again. Each node reads and writes the same 19 locations, so one array suffices.
-template <typename S, bool RESID, int MODE>
+// GEOM: the lattice may have a geometry (solid nodes, on-site rules) and a body force;
+// the plain variant reads neither.
+template <typename S, bool RESID, int MODE, bool GEOM = false>
 __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
   using T = typename ComputeOf<S>::T;
   const uint32_t cell = blk * SWEEP_THREADS + threadIdx.x;
@@ -521,10 +625,11 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
       const uint32_t sz = cz(k) > 0 ? zm : (cz(k) < 0 ? zp : z);
       return (sz * a.ny + sy) * a.nx + sx;
     };
-    // solid-node links (A/B lattices with solid nodes only; 0 everywhere else)
-    const uint32_t lm = (MODE == STREAM_AB && a.links) ? __ldg(a.links + cell) : 0u;
+    // geometry word (A/B lattices with a geometry only; 0 everywhere else)
+    uint32_t lm = 0u;
+    if constexpr (GEOM) lm = a.links ? __ldg(a.links + cell) : 0u;
     T h[Q];
-    if (lm == 0u) {
+    if (!GEOM || (lm & ~(RULE_BITS << RULE_SHIFT)) == 0u) {
       static_for<0, Q>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
         if constexpr (MODE == STREAM_AB) {
@@ -550,13 +655,45 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
       });
     }
     const bool solid = (lm & SOLID_NODE) != 0u;
+    const uint32_t rule = (lm >> RULE_SHIFT) & RULE_BITS;
     const int fx = px ? 0 : (x == 0 ? 1 : (x == a.nx - 1 ? 2 : 0));
     const int fy = py ? 0 : (y == 0 ? 1 : (y == a.ny - 1 ? 2 : 0));
     const int fz = pz ? 0 : (z == 0 ? 1 : (z == a.nz - 1 ? 2 : 0));
     const int code = fx + 3 * fy + 9 * fz;
-    if (code != 0 && !solid) apply_boundary(code, a, x, y, z, h);
-    const Moments<T> m = moments(h, rho0_of<T>(a));
-    if constexpr (RESID) residual_terms(m, ref_rho<S>(a.rho0), static_cast<T*>(a.snap), a.N, cell, red);
+    if constexpr (GEOM) {
+      if (rule != 0u) apply_rule<1, 62>(rule, h, ref_density<T>(a));
+      else if (code != 0 && !solid) apply_boundary(code, a, x, y, z, h);
+    } else {
+      if (code != 0) apply_boundary(code, a, x, y, z, h);
+    }
+    Moments<T> m = moments(h, rho0_of<T>(a));
+    if constexpr (GEOM) {
+      if (a.forced && !solid) {
+        // eq. gravity: the collision relaxes toward the equilibrium at u + tau F / rho
+        // and so adds F to the momentum; the residual sees the stored velocity
+        const T inv = T(1) / m.rho;
+        if constexpr (RESID) {
+          Moments<T> mp = m;
+          mp.jx += force_of<T>(a, 0);
+          mp.jy += force_of<T>(a, 1);
+          mp.jz += force_of<T>(a, 2);
+          mp.ux = mp.jx * inv;
+          mp.uy = mp.jy * inv;
+          mp.uz = mp.jz * inv;
+          residual_terms(mp, ref_rho<S>(a.rho0), static_cast<T*>(a.snap), a.N, cell, red);
+        }
+        m.jx += tforce_of<T>(a, 0);
+        m.jy += tforce_of<T>(a, 1);
+        m.jz += tforce_of<T>(a, 2);
+        m.ux = m.jx * inv;
+        m.uy = m.jy * inv;
+        m.uz = m.jz * inv;
+      } else if constexpr (RESID) {
+        residual_terms(m, ref_rho<S>(a.rho0), static_cast<T*>(a.snap), a.N, cell, red);
+      }
+    } else if constexpr (RESID) {
+      residual_terms(m, ref_rho<S>(a.rho0), static_cast<T*>(a.snap), a.N, cell, red);
+    }
     if (!solid) collide(h, m, omega_of<T>(a));
     static_for<0, Q>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
@@ -586,20 +723,22 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
 // FP64 pipe and get room for their double registers.
 // The AA gather-scatter step also keeps its push targets and takes 2 blocks fewer, the
 // AA in-place step one fewer.
-template <typename S, bool RESID, bool BATCHED, int MODE>
+// The general-geometry variant (GEOM) carries the rule dispatch and the force and is
+// compiled for 4 blocks (2 for FP64).
+template <typename S, bool RESID, bool BATCHED, int MODE, bool GEOM = false>
 struct SweepOccupancy {
   static constexpr int base = BATCHED ? 4 : (RESID ? 5 : 6);
-  static constexpr int blocks = MODE == 1 ? (base > 4 ? 4 : base - 1) : (MODE == 2 ? (base > 5 ? 5 : base) : base);
+  static constexpr int blocks = GEOM ? 4 : (MODE == 1 ? (base > 4 ? 4 : base - 1) : (MODE == 2 ? (base > 5 ? 5 : base) : base));
 };
-template <bool RESID, bool BATCHED, int MODE>
-struct SweepOccupancy<double, RESID, BATCHED, MODE> {
-  static constexpr int blocks = (RESID && BATCHED) || MODE == 1 ? 2 : 3;
+template <bool RESID, bool BATCHED, int MODE, bool GEOM>
+struct SweepOccupancy<double, RESID, BATCHED, MODE, GEOM> {
+  static constexpr int blocks = (RESID && BATCHED) || MODE == 1 || GEOM ? 2 : 3;
 };
 
-template <typename S, bool RESID, int MODE>
-__global__ void __launch_bounds__(SWEEP_THREADS, (SweepOccupancy<S, RESID, false, MODE>::blocks))
+template <typename S, bool RESID, int MODE, bool GEOM>
+__global__ void __launch_bounds__(SWEEP_THREADS, (SweepOccupancy<S, RESID, false, MODE, GEOM>::blocks))
     sweep_kernel(const __grid_constant__ SweepArgs a) {
-  sweep_block<S, RESID, MODE>(a, blockIdx.x);
+  sweep_block<S, RESID, MODE, GEOM>(a, blockIdx.x);
 }
 
 // One time step of every lattice of a batch. A persistent grid splits the batch's
@@ -651,7 +790,12 @@ __global__ void __launch_bounds__(SWEEP_THREADS, (SweepOccupancy<S, RESID, true,
       lat_end = e->block_begin + e->nblocks;
       __syncthreads();
     }
-    sweep_block<S, RESID, MODE>(sa, b - lat_begin);
+    if constexpr (MODE == STREAM_AB) {
+      if (sa.links || sa.forced) sweep_block<S, RESID, MODE, true>(sa, b - lat_begin);
+      else sweep_block<S, RESID, MODE, false>(sa, b - lat_begin);
+    } else {
+      sweep_block<S, RESID, MODE, false>(sa, b - lat_begin);
+    }
     if constexpr (RESID) __syncthreads();  // the block-sum buffer is reused by the next block
     ++b;
   }
@@ -715,18 +859,19 @@ __global__ void __launch_bounds__(SWEEP_THREADS)
 // ---------------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------------
-template <typename S, int MODE>
+template <typename S, int MODE, bool GEOM>
 void launch_sweep_mode(const SweepArgs& a, bool resid, cudaStream_t s) {
   const uint32_t blocks = sweep_blocks(a.N);
-  if (resid) sweep_kernel<S, true, MODE><<<blocks, SWEEP_THREADS, 0, s>>>(a);
-  else sweep_kernel<S, false, MODE><<<blocks, SWEEP_THREADS, 0, s>>>(a);
+  if (resid) sweep_kernel<S, true, MODE, GEOM><<<blocks, SWEEP_THREADS, 0, s>>>(a);
+  else sweep_kernel<S, false, MODE, GEOM><<<blocks, SWEEP_THREADS, 0, s>>>(a);
 }
 
 template <typename S>
 cudaError_t launch_sweep_impl(const SweepArgs& a, bool resid, int mode, cudaStream_t s) {
-  if (mode == STREAM_AA_GATHER) launch_sweep_mode<S, STREAM_AA_GATHER>(a, resid, s);
-  else if (mode == STREAM_AA_LOCAL) launch_sweep_mode<S, STREAM_AA_LOCAL>(a, resid, s);
-  else launch_sweep_mode<S, STREAM_AB>(a, resid, s);
+  if (mode == STREAM_AA_GATHER) launch_sweep_mode<S, STREAM_AA_GATHER, false>(a, resid, s);
+  else if (mode == STREAM_AA_LOCAL) launch_sweep_mode<S, STREAM_AA_LOCAL, false>(a, resid, s);
+  else if (a.links || a.forced) launch_sweep_mode<S, STREAM_AB, true>(a, resid, s);
+  else launch_sweep_mode<S, STREAM_AB, false>(a, resid, s);
   return cudaGetLastError();
 }
 

@@ -65,11 +65,20 @@ struct SweepArgs {
   FaceBC face[6];
   void* snap;         // residual steps: [3][N] velocity snapshot in the compute type
   double* partials;   // residual steps: [blocks][4] per-block sums
-  const uint32_t* links;  // optional [N]: bit k = the pull source of population k is
-                          // solid, bit 31 = the node is solid (nullptr: no solid nodes)
+  const uint32_t* links;  // optional [N] geometry words (nullptr: no geometry), see below
+  uint32_t forced;        // nonzero: a body force acts (eq. gravity)
+  double force[3];        // F: momentum the collision adds per step
+  double tforce[3];       // tau F: the equilibrium velocity shift times rho
+  float forcef[3], tforcef[3];
 };
 
+// Geometry word of a node: bits 0..18 (nodes without a rule): the pull source of
+// population k is solid (mid-grid bounce-back); bits 24..29: the node's on-site rule
+// (0: none; 1..50: the C ABI codes of planes, concave edges, corners and junctions;
+// 51..62: the convex edges -7..-18 as 44 - code); bit 31: the node is solid.
 constexpr uint32_t SOLID_NODE = 1u << 31;
+constexpr int RULE_SHIFT = 24;
+constexpr uint32_t RULE_BITS = 0x3fu;
 
 // One lattice of a batch, as the batched sweep reads it from device memory.
 struct BatchEntry {

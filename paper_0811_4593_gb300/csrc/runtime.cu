@@ -546,27 +546,77 @@ lbm_status lbm_get_populations(lbm_ctx* ctx, void* dst, int z0, int nzs, lbm_mem
   return copy_populations(ctx, dst, z0, nzs, where, false);
 }
 
-lbm_status lbm_set_solid(lbm_ctx* ctx, const uint8_t* solid) {
+}  // extern "C"
+
+// Populations the on-site rule of a node code overwrites (bit k: population k), or 0
+// for a value that is not a code. The codes name the normal by a lattice-vector index
+// (include/lbm.h): planes 1..6, concave edges 7..18, convex edges -7..-18, corners
+// 19..26, convex-edge/plane junctions 27..50.
+static uint32_t rule_unknowns(int code) {
+  auto dot = [](int k, const int* v) { return lbm::cx(k) * v[0] + lbm::cy(k) * v[1] + lbm::cz(k) * v[2]; };
+  auto vec = [](int k, int* v) { v[0] = lbm::cx(k); v[1] = lbm::cy(k); v[2] = lbm::cz(k); };
+  uint32_t m = 0;
+  const int ac = code < 0 ? -code : code;
+  if (code >= 1 && code <= 6) {
+    int n[3];
+    vec(code - 1, n);
+    for (int k = 0; k < 19; ++k)
+      if (dot(k, n) > 0) m |= 1u << k;
+  } else if (ac >= 7 && ac <= 18) {
+    int d[3];
+    vec(ac - 1, d);
+    for (int k = 0; k < 19; ++k) {
+      if (code > 0) {
+        // concave: from beyond either plane (normals = the axis parts of d)
+        const bool b = (d[0] && lbm::cx(k) * d[0] > 0) || (d[1] && lbm::cy(k) * d[1] > 0) ||
+                       (d[2] && lbm::cz(k) * d[2] > 0);
+        if (b) m |= 1u << k;
+      } else if (lbm::cx(k) == d[0] && lbm::cy(k) == d[1] && lbm::cz(k) == d[2]) {
+        m |= 1u << k;  // convex: only c = d comes from the solid quadrant
+      }
+    }
+  } else if (code >= 19 && code <= 26) {
+    const int b = code - 19;
+    const int sx = (b & 1) ? -1 : 1, sy = (b & 2) ? -1 : 1, sz = (b & 4) ? -1 : 1;
+    for (int k = 0; k < 19; ++k)
+      if (lbm::cx(k) * sx > 0 || lbm::cy(k) * sy > 0 || lbm::cz(k) * sz > 0) m |= 1u << k;
+  } else if (code >= 27 && code <= 50) {
+    int n[3];
+    vec((code - 27) / 4, n);
+    const int kd = lbm::junction_diagonal((code - 27) / 4, (code - 27) % 4);
+    for (int k = 0; k < 19; ++k)
+      if (dot(k, n) > 0 || k == kd) m |= 1u << k;
+  }
+  return m;
+}
+
+extern "C" {
+
+lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* solid, const int8_t* code) {
   if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
-  if (!solid) return fail(ctx, LBM_ERR_ARG, "solid is NULL");
-  if (ctx->scheme != LBM_SCHEME_AB) return fail(ctx, LBM_ERR_ARG, "solid nodes need the A/B scheme");
+  if (!solid && !code) return fail(ctx, LBM_ERR_ARG, "solid and code are both NULL");
+  if (ctx->scheme != LBM_SCHEME_AB) return fail(ctx, LBM_ERR_ARG, "a geometry needs the A/B scheme");
+  if (ctx->batch) return fail(ctx, LBM_ERR_STATE, "detach the context from its batch first");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, LBM_ERR_CUDA, "cannot make device %d current", ctx->device);
   if (lbm_status st0 = settle(ctx); st0 != LBM_OK) return st0;
-  // bit k: the node population k is pulled from (x - c_k, wrapped on periodic axes) is
-  // solid; bit 31: the node is solid. Sources outside a walled axis stay unflagged (the
-  // boundary closure fills those populations).
+  // Geometry word per node (lbm_internal.h): solid nodes are flagged; a node with a
+  // code gets its rule and must be able to stream everything its rule leaves alone;
+  // any other node takes mid-grid bounce-back from its solid neighbours. Sources
+  // outside a walled axis stay unflagged on code-0 nodes (the box closure fills them).
   const int nx = ctx->nx, ny = ctx->ny, nz = ctx->nz;
+  const int dims[3] = {nx, ny, nz};
   const uint32_t per = ctx->args.periodic;
   std::vector<uint32_t> links(ctx->N, 0u);
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
         const size_t node = (size_t(z) * ny + y) * nx + x;
-        uint32_t m = solid[node] ? lbm::SOLID_NODE : 0u;
+        const bool is_solid = solid && solid[node];
+        const int c = code ? code[node] : 0;
+        uint32_t blocked = 0, from_solid = 0;
         for (int k = 0; k < 19; ++k) {
           int p[3] = {x - lbm::cx(k), y - lbm::cy(k), z - lbm::cz(k)};
-          const int dims[3] = {nx, ny, nz};
           bool inside = true;
           for (int a = 0; a < 3; ++a) {
             if (p[a] < 0 || p[a] >= dims[a]) {
@@ -574,21 +624,63 @@ lbm_status lbm_set_solid(lbm_ctx* ctx, const uint8_t* solid) {
               p[a] = (p[a] % dims[a] + dims[a]) % dims[a];
             }
           }
-          if (inside && solid[(size_t(p[2]) * ny + p[1]) * nx + p[0]]) m |= 1u << k;
+          const bool s_solid = inside && solid && solid[(size_t(p[2]) * ny + p[1]) * nx + p[0]];
+          if (s_solid) from_solid |= 1u << k;
+          if (s_solid || !inside) blocked |= 1u << k;
         }
-        links[node] = m;
+        if (c == 0) {
+          links[node] = is_solid ? lbm::SOLID_NODE : from_solid;
+          continue;
+        }
+        const uint32_t rule_mask = rule_unknowns(c);
+        if (!rule_mask) return fail(ctx, LBM_ERR_ARG, "node (%d, %d, %d): %d is not a boundary code", x, y, z, c);
+        if (is_solid) return fail(ctx, LBM_ERR_ARG, "node (%d, %d, %d) is solid and has code %d", x, y, z, c);
+        if (blocked & ~rule_mask)
+          return fail(ctx, LBM_ERR_ARG,
+                      "node (%d, %d, %d): code %d leaves a population from a solid or outside node unset", x,
+                      y, z, c);
+        const uint32_t rule = c > 0 ? uint32_t(c) : uint32_t(44 - c);
+        links[node] = rule << lbm::RULE_SHIFT;
       }
   if (!ctx->args.links) {
     void* d = ctx_alloc(ctx, sizeof(uint32_t) * ctx->N);
-    if (!d) return fail(ctx, LBM_ERR_OOM, "allocation of the solid-link mask failed");
+    if (!d) return fail(ctx, LBM_ERR_OOM, "allocation of the geometry words failed");
     ctx->args.links = static_cast<const uint32_t*>(d);
   }
   LBM_CUDA(ctx, cudaMemcpyAsync(const_cast<uint32_t*>(ctx->args.links), links.data(), sizeof(uint32_t) * ctx->N,
-                                cudaMemcpyHostToDevice, ctx->stream), "uploading the solid-link mask");
+                                cudaMemcpyHostToDevice, ctx->stream), "uploading the geometry words");
   // solid nodes are carried unchanged from buffer to buffer: start both alike
   LBM_CUDA(ctx, cudaMemcpyAsync(ctx->buf[ctx->cur ^ 1], ctx->buf[ctx->cur], 19ull * ctx->N * storage_bytes(ctx->prec),
                                 cudaMemcpyDeviceToDevice, ctx->stream), "copying the state");
   LBM_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "synchronising");
+  return LBM_OK;
+}
+
+lbm_status lbm_set_solid(lbm_ctx* ctx, const uint8_t* solid) {
+  if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+  if (!solid) return fail(ctx, LBM_ERR_ARG, "solid is NULL");
+  return lbm_set_geometry(ctx, solid, nullptr);
+}
+
+lbm_status lbm_set_body_force(lbm_ctx* ctx, const double force[3]) {
+  if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+  if (!force) return fail(ctx, LBM_ERR_ARG, "force is NULL");
+  if (!std::isfinite(force[0]) || !std::isfinite(force[1]) || !std::isfinite(force[2]))
+    return fail(ctx, LBM_ERR_ARG, "force is not finite");
+  if (ctx->scheme != LBM_SCHEME_AB) return fail(ctx, LBM_ERR_ARG, "a body force needs the A/B scheme");
+  if (ctx->batch) return fail(ctx, LBM_ERR_STATE, "detach the context from its batch first");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, LBM_ERR_CUDA, "cannot make device %d current", ctx->device);
+  if (lbm_status st0 = settle(ctx); st0 != LBM_OK) return st0;
+  lbm::SweepArgs& a = ctx->args;
+  const double tau = 1.0 / a.omega;
+  for (int i = 0; i < 3; ++i) {
+    a.force[i] = force[i];
+    a.tforce[i] = tau * force[i];
+    a.forcef[i] = float(force[i]);
+    a.tforcef[i] = float(a.tforce[i]);
+  }
+  a.forced = (force[0] != 0.0 || force[1] != 0.0 || force[2] != 0.0) ? 1u : 0u;
   return LBM_OK;
 }
 

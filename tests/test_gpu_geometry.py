@@ -50,3 +50,144 @@ def test_solid_nodes_need_the_ab_scheme():
     with lbm.Lattice(wl.nx, wl.ny, wl.nz, wl.tau, [None] * 4 + wl.utabs[4:], "f32", scheme="aa") as lat:
         with pytest.raises(lbm.LBMError):
             lat.set_solid(wl.solid)
+
+
+# ---------------------------------------------------------------------------------
+# General geometry (per-node on-site rules) and body force.
+# ---------------------------------------------------------------------------------
+
+def pillar(axis):
+    flow = [a for a in range(3) if a != axis][0]
+    return inp.pillar_channel(axis=axis, flow=flow)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_pillar_rules_match_oracle(axis, prec):
+    # the three pillar orientations use every plane, concave-edge, convex-edge and
+    # junction code; the force is ten times the workload's so that it shows in 30 steps
+    wl = pillar(axis)
+    wl.force = 10.0 * wl.force
+    f0 = noisy_state((19, wl.nz, wl.ny, wl.nx), 80 + axis, amp=0.01, u=(0.003, -0.002, 0.001))
+    got, ref = run_pair(wl, prec, f0, 30)
+    fluid = wl.solid == 0
+    assert velocity_error(wl, got, ref) <= TOL[prec]
+    if prec == "f64":
+        assert np.abs(got - ref)[:, fluid].max() / np.abs(ref).max() <= 1e-12
+    start = decode(encode(f0, prec), prec)
+    np.testing.assert_array_equal(got[:, ~fluid], start[:, ~fluid])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_corner_codes_equal_box_corners_bitwise(prec):
+    # a closed box with its walls moved inside as coded nodes (planes, concave edges,
+    # corners) evolves to the same bits as the box with no-slip faces
+    import paper_0811_4593_gb300 as lbm
+    box = inp.make_workload("box", 11, 9, 7, 0.8, [inp.ZERO] * 6)
+    box.force = np.array([4e-5, -2e-5, 1e-5])
+    emb = inp.embedded_walls(box)
+    f0 = noisy_state((19, box.nz, box.ny, box.nx), 31, amp=0.01)
+    g0 = noisy_state((19, emb.nz, emb.ny, emb.nx), 32, amp=0.0)
+    g0[:, 1:-1, 1:-1, 1:-1] = f0
+    with lbm.Lattice.from_workload(box, prec) as a, lbm.Lattice.from_workload(emb, prec) as b:
+        a.set_populations(encode(f0, prec))
+        b.set_populations(encode(g0, prec))
+        a.step(40)
+        b.step(40)
+        np.testing.assert_array_equal(b.get_populations()[:, 1:-1, 1:-1, 1:-1], a.get_populations())
+
+
+@pytest.mark.parametrize("prec,tau,steps", [("f64", 2.0, 7000), ("f64", 1.0, 20000), ("f32", 2.0, 7000)])
+def test_body_force_poiseuille_32_cubed(prec, tau, steps):
+    # the paper's body-force check: 32^3, walls on the x faces, periodic y and z; the
+    # velocity after the boundary rule is the parabola of eq. poiseuille with the
+    # viscosity of eq. visc and zero on the wall nodes
+    import paper_0811_4593_gb300 as lbm
+    wl = inp.force_poiseuille(n=32, tau=tau, force=1e-6, wall_axis=0, flow_axis=2, other=None)
+    with lbm.Lattice.from_workload(wl, prec) as lat:
+        lat.step(steps)
+        rho, u = lat.macros()
+        rho, u = rho.double().cpu().numpy(), u.double().cpu().numpy()
+    F = wl.force[2]
+    u_pre = u[2] - F / rho
+    x = np.arange(wl.nx)
+    h = (wl.nx - 1) / 2.0
+    exact = F / (2.0 * rho * (tau - 0.5) / 3.0) * (h * h - (x - h) ** 2)
+    err = np.abs(u_pre - exact).max() / exact.max()
+    assert err < (1e-9 if prec == "f64" else 1e-4), err
+    assert np.abs(u_pre[:, :, [0, -1]]).max() < (1e-15 if prec == "f64" else 1e-7)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_force_residual_matches_oracle(prec):
+    import oracle
+    import paper_0811_4593_gb300 as lbm
+    wl = pillar(2)
+    f0 = noisy_state((19, wl.nz, wl.ny, wl.nx), 12, amp=0.01)
+    s0 = encode(f0, prec)
+    olat = oracle.Lattice.from_workload(wl)
+    ref = oracle.run(olat, decode(s0, prec), 9)
+    _, u9 = oracle.macros(olat, ref)
+    ref10 = oracle.run(olat, ref, 1)
+    mass_ref, du2, u2, _ = oracle.reduce(olat, ref10, u9)
+    with lbm.Lattice.from_workload(wl, prec) as lat:
+        lat.set_populations(s0)
+        lat.step(8)
+        lat.step_residual(1)      # snapshot of the stored velocity after step 9
+        r, m = lat.step_residual(1)
+    assert abs(m - mass_ref) / mass_ref < (1e-13 if prec == "f64" else 1e-6)
+    assert abs(r - np.sqrt(du2 / u2)) / np.sqrt(du2 / u2) < (1e-9 if prec == "f64" else 2e-2)
+
+
+def test_geometry_in_a_batch_matches_solo_runs():
+    import paper_0811_4593_gb300 as lbm
+    wls = [pillar(0), inp.force_poiseuille(n=12, tau=0.9, force=1e-5, other=5), inp.couette()]
+    solo = []
+    for i, wl in enumerate(wls):
+        with lbm.Lattice.from_workload(wl, "f32") as lat:
+            lat.set_populations(encode(noisy_state((19, wl.nz, wl.ny, wl.nx), 40 + i, amp=0.01), "f32"))
+            lat.step(12)
+            solo.append(lat.get_populations())
+    with lbm.Batch(3, "f32") as b:
+        lats = []
+        for i, wl in enumerate(wls):
+            lat = lbm.Lattice.from_workload(wl, "f32")
+            lat.set_populations(encode(noisy_state((19, wl.nz, wl.ny, wl.nx), 40 + i, amp=0.01), "f32"))
+            b.attach(i, lat)
+            lats.append(lat)
+        with pytest.raises(lbm.LBMError):
+            lats[2].set_body_force((1e-5, 0.0, 0.0))     # attached: detach first
+        b.step(12)
+        for lat, ref in zip(lats, solo):
+            np.testing.assert_array_equal(lat.get_populations(), ref)
+        for lat in lats:
+            lat.close()
+
+
+def test_inconsistent_codes_are_rejected_by_the_library():
+    import paper_0811_4593_gb300 as lbm
+    wl = pillar(2)
+    bad = wl.code.copy()
+    node = tuple(np.argwhere(bad == -12)[0])
+    bad[node] = -7
+    with lbm.Lattice(wl.nx, wl.ny, wl.nz, wl.tau, wl.utabs, "f32") as lat:
+        with pytest.raises(lbm.LBMError, match="leaves a population"):
+            lat.set_geometry(wl.solid, bad)
+        bad2 = wl.code.copy()
+        bad2[0, 0, 0] = 60
+        with pytest.raises(lbm.LBMError, match="not a boundary code"):
+            lat.set_geometry(wl.solid, bad2)
+        bad3 = wl.code.copy()
+        bad3[tuple(np.argwhere(wl.solid == 1)[0])] = 1
+        with pytest.raises(lbm.LBMError, match="is solid"):
+            lat.set_geometry(wl.solid, bad3)
+        with pytest.raises(lbm.LBMError):
+            lat.set_body_force((float("nan"), 0.0, 0.0))
+        lat.set_geometry(wl.solid, wl.code)
+        lat.set_body_force(wl.force)
+        lat.step(2)
+    with lbm.Lattice(wl.nx, wl.ny, wl.nz, wl.tau, wl.utabs, "f32", scheme="aa") as lat:
+        with pytest.raises(lbm.LBMError):
+            lat.set_geometry(wl.solid, wl.code)
+        with pytest.raises(lbm.LBMError):
+            lat.set_body_force(wl.force)
