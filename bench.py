@@ -256,6 +256,14 @@ def profiled_fp64_per_node(wl_name: str):
     return rec.get("fp64_inst_per_node") if rec.get("source_sha") == sweep_source_hash() else None
 
 
+def sweep_kernel_name(wl, precision, scheme="ab"):
+    """The kernel that runs the plain (non-residual) steps of a lattice."""
+    if precision == "f16" and scheme == "ab" and wl.nx % 2 == 0 and getattr(wl, "solid", None) is None \
+            and getattr(wl, "force", None) is None:
+        return "sweep_pair_kernel<f16>"
+    return f"sweep_kernel<{precision}>"
+
+
 def run_variant(wl, precision, steps, warmup, resid_every, dist_ctx, clocks=None, scheme="ab"):
     import torch
 
@@ -267,6 +275,7 @@ def run_variant(wl, precision, steps, warmup, resid_every, dist_ctx, clocks=None
     out = {"mlups": wl.cells * steps / (total_ms * 1e-3) / 1e6, "ms_per_step": total_ms / steps,
            "sweep_ms": step_ms, "achieved_gbs": ach, "frac": ach / hbm, "steps": steps,
            "bytes_per_update": BYTES_PER_UPDATE[precision], "scheme": scheme,
+           "kernel": sweep_kernel_name(wl, precision, scheme),
            "resident_bytes_per_node": BYTES_PER_UPDATE[precision] // (2 if scheme == "aa" else 1)}
     if precision == "f64":
         # the FP64 sweep is bound by the FP64 pipe, not by HBM
@@ -363,7 +372,7 @@ def native(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "peak_source": hbm_src,
                      "traffic": profiled_traffic("sweep", args.precision, args.workload),
-                     "kernel": f"sweep_kernel<{args.precision}>",
+                     "kernel": sweep_kernel_name(wl, args.precision),
                      "bytes_per_update": BYTES_PER_UPDATE[args.precision], "updates_per_launch": wl.cells,
                      "sweep_ms": round(sweep_ms, 4)},
         "gpu_launches": launches,

@@ -472,22 +472,27 @@ struct Moments {
 
 template <typename T>
 __device__ __forceinline__ Moments<T> moments(const T (&h)[Q], T rho0) {
-  T d = T(0), jx = T(0), jy = T(0), jz = T(0);
+  // the populations with c_x = +1, -1 and 0 are summed apart, so that the density and
+  // the x momentum share the three partial sums (37 additions instead of 45)
+  T sp = T(0), sm = T(0), s0 = T(0), jy = T(0), jz = T(0);
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    d += h[k];
-    if constexpr (cx(k) != 0) jx += T(cx(k)) * h[k];
-    if constexpr (cy(k) != 0) jy += T(cy(k)) * h[k];
-    if constexpr (cz(k) != 0) jz += T(cz(k)) * h[k];
+    if constexpr (cx(k) > 0) sp += h[k];
+    else if constexpr (cx(k) < 0) sm += h[k];
+    else s0 += h[k];
+    if constexpr (cy(k) > 0) jy += h[k];
+    else if constexpr (cy(k) < 0) jy -= h[k];
+    if constexpr (cz(k) > 0) jz += h[k];
+    else if constexpr (cz(k) < 0) jz -= h[k];
   });
   Moments<T> m;
-  m.drho = d;
-  m.rho = rho0 + d;
-  m.jx = jx;
+  m.drho = (sp + sm) + s0;
+  m.rho = rho0 + m.drho;
+  m.jx = sp - sm;
   m.jy = jy;
   m.jz = jz;
   const T inv = T(1) / m.rho;
-  m.ux = jx * inv;
+  m.ux = m.jx * inv;
   m.uy = jy * inv;
   m.uz = jz * inv;
   return m;
@@ -498,26 +503,32 @@ __device__ __forceinline__ Moments<T> moments(const T (&h)[Q], T rho0) {
 //   v^eq_{+-i} = w_i (b + s_i +- a_i),  b = drho - 3/2 j.u,  s_i = 9/2 (c_i.j)(c_i.u),
 //   a_i = 3 c_i.j
 // (j = rho u), which equals w_i (drho + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u^2)) (eq. feq)
-// term by term and shares the symmetric part between the two populations.
+// term by term and shares the symmetric part between the two populations. omega w_i is
+// folded into the per-class factors, so a pair costs two products, one fused
+// multiply-add, two additions and two fused relaxations.
 template <typename T>
 __device__ __forceinline__ void collide(T (&h)[Q], const Moments<T>& m, T omega) {
   const T b = m.drho - T(1.5) * (m.jx * m.ux + m.jy * m.uy + m.jz * m.uz);
   const T keep = T(1) - omega;
+  const T ow_axis = omega * wgt<T>(0), ow_diag = omega * wgt<T>(6);
+  const T ob_axis = ow_axis * b, ob_diag = ow_diag * b;
+  const T g_axis = T(4.5) * ow_axis, g_diag = T(4.5) * ow_diag;
+  const T a_axis = T(3) * ow_axis, a_diag = T(3) * ow_diag;
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     constexpr int o = opp(k);
     if constexpr (k == Q - 1) {
       h[k] = keep * h[k] + (omega * wgt<T>(k)) * b;
     } else if constexpr (k < o) {
+      constexpr bool axis = w36(k) == 2;
       T cj = T(0), cu = T(0);
       if constexpr (cx(k) != 0) { cj += T(cx(k)) * m.jx; cu += T(cx(k)) * m.ux; }
       if constexpr (cy(k) != 0) { cj += T(cy(k)) * m.jy; cu += T(cy(k)) * m.uy; }
       if constexpr (cz(k) != 0) { cj += T(cz(k)) * m.jz; cu += T(cz(k)) * m.uz; }
-      const T t = b + T(4.5) * cj * cu;
-      const T a = T(3) * cj;
-      const T ow = omega * wgt<T>(k);
-      h[k] = keep * h[k] + ow * (t + a);
-      h[o] = keep * h[o] + ow * (t - a);
+      const T t = (axis ? g_axis : g_diag) * cj * cu + (axis ? ob_axis : ob_diag);
+      const T a = (axis ? a_axis : a_diag) * cj;
+      h[k] = keep * h[k] + (t + a);
+      h[o] = keep * h[o] + (t - a);
     }
   });
 }
@@ -741,6 +752,83 @@ __global__ void __launch_bounds__(SWEEP_THREADS, (SweepOccupancy<S, RESID, false
   sweep_block<S, RESID, MODE, GEOM>(a, blockIdx.x);
 }
 
+// ---------------------------------------------------------------------------------
+// Paired binary16 sweep: the plain A/B step (no residual, no geometry, no force) of a
+// binary16 lattice with even nx, two neighbouring nodes (x0, x0 + 1), x0 even, per
+// thread. The binary16 sweep moves half the bytes of the float one for the same
+// arithmetic and is bound by instruction issue; pairing halves the index and address
+// work per node: a population with c_x = 0 is read as one aligned half2 for both
+// nodes, one with c_x != 0 as two halves from one address, and the two results of a
+// population are stored as one half2. Each node runs the single-node sweep's closure,
+// moment and collision code, so both sweeps give the same bits.
+// ---------------------------------------------------------------------------------
+template <bool FAST>
+__device__ __forceinline__ void load_pair(const SweepArgs& a, uint32_t x0, uint32_t xam, uint32_t xbp,
+                                          const uint32_t (&rows)[3][3], float (&hA)[Q], float (&hB)[Q]) {
+  static_for<0, Q>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    const __half* base = static_cast<const __half*>(a.src_pop[k]) + rows[1 - cz(k)][1 - cy(k)];
+    if constexpr (cx(k) == 0) {
+      const __half2 v = __ldg(reinterpret_cast<const __half2*>(base + x0));
+      hA[k] = __low2float(v);
+      hB[k] = __high2float(v);
+    } else if constexpr (cx(k) > 0) {  // pulled from x - 1
+      const __half* pb = base + x0;
+      hB[k] = __half2float(__ldg(pb));
+      hA[k] = __half2float(__ldg(FAST ? pb - 1 : base + xam));
+    } else {  // pulled from x + 1
+      const __half* pa = base + x0 + 1;
+      hA[k] = __half2float(__ldg(pa));
+      hB[k] = __half2float(__ldg(FAST ? pa + 1 : base + xbp));
+    }
+  });
+}
+
+template <typename S>
+__global__ void __launch_bounds__(SWEEP_THREADS, 4) sweep_pair_kernel(const __grid_constant__ SweepArgs a) {
+  static_assert(std::is_same<S, __half>::value, "the paired sweep is for binary16 storage");
+  const uint32_t pair = blockIdx.x * SWEEP_THREADS + threadIdx.x;
+  if (pair >= (a.N >> 1)) return;
+  const uint32_t q1 = fdiv(a.div_nxh, pair);
+  const uint32_t x0 = 2u * (pair - q1 * (a.nx >> 1));
+  const uint32_t z = fdiv(a.div_ny, q1);
+  const uint32_t y = q1 - z * a.ny;
+  const uint32_t cell = q1 * a.nx + x0;
+  const bool px = a.periodic & 1u, py = a.periodic & 2u, pz = a.periodic & 4u;
+  const uint32_t ym = y ? y - 1 : (py ? a.ny - 1 : 0);
+  const uint32_t yp = (y + 1 < a.ny) ? y + 1 : (py ? 0 : a.ny - 1);
+  const uint32_t zm = z ? z - 1 : (pz ? a.nz - 1 : 0);
+  const uint32_t zp = (z + 1 < a.nz) ? z + 1 : (pz ? 0 : a.nz - 1);
+  // rows[1 - c_z][1 - c_y]: start of the row a population is pulled from
+  const uint32_t zs[3] = {zm, z, zp}, ys[3] = {ym, y, yp};
+  uint32_t rows[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) rows[i][j] = (zs[i] * a.ny + ys[j]) * a.nx;
+  // source x of node A for c_x = +1 and of node B for c_x = -1 (clamped outside a
+  // walled axis: those populations are unknown and overwritten by the closure)
+  const uint32_t xam = x0 ? x0 - 1 : (px ? a.nx - 1 : 0);
+  const uint32_t xbp = (x0 + 2 < a.nx) ? x0 + 2 : (px ? 0 : a.nx - 1);
+  float hA[Q], hB[Q];
+  if (x0 != 0 && x0 + 2 < a.nx) load_pair<true>(a, x0, xam, xbp, rows, hA, hB);
+  else load_pair<false>(a, x0, xam, xbp, rows, hA, hB);
+  const int fy = py ? 0 : (y == 0 ? 1 : (y == a.ny - 1 ? 2 : 0));
+  const int fz = pz ? 0 : (z == 0 ? 1 : (z == a.nz - 1 ? 2 : 0));
+  const int codeA = (px ? 0 : (x0 == 0 ? 1 : 0)) + 3 * fy + 9 * fz;
+  const int codeB = (px ? 0 : (x0 + 1 == a.nx - 1 ? 2 : 0)) + 3 * fy + 9 * fz;
+  if (codeA != 0) apply_boundary(codeA, a, x0, y, z, hA);
+  if (codeB != 0) apply_boundary(codeB, a, x0 + 1, y, z, hB);
+  const Moments<float> mA = moments(hA, a.rho0f);
+  collide(hA, mA, a.omegaf);
+  const Moments<float> mB = moments(hB, a.rho0f);
+  collide(hB, mB, a.omegaf);
+  static_for<0, Q>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    *reinterpret_cast<__half2*>(static_cast<__half*>(a.dst_pop[k]) + cell) = __floats2half2_rn(hA[k], hB[k]);
+  });
+}
+
 // One time step of every lattice of a batch. A persistent grid splits the batch's
 // global block range into one contiguous share per CTA; a CTA caches the descriptor of
 // the lattice it is in (in shared memory) and runs the same per-block code as the
@@ -868,6 +956,12 @@ void launch_sweep_mode(const SweepArgs& a, bool resid, cudaStream_t s) {
 
 template <typename S>
 cudaError_t launch_sweep_impl(const SweepArgs& a, bool resid, int mode, cudaStream_t s) {
+  if constexpr (std::is_same<S, __half>::value) {
+    if (mode == STREAM_AB && !resid && !a.links && !a.forced && (a.nx & 1u) == 0) {
+      sweep_pair_kernel<S><<<sweep_blocks(a.N >> 1), SWEEP_THREADS, 0, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
   if (mode == STREAM_AA_GATHER) launch_sweep_mode<S, STREAM_AA_GATHER, false>(a, resid, s);
   else if (mode == STREAM_AA_LOCAL) launch_sweep_mode<S, STREAM_AA_LOCAL, false>(a, resid, s);
   else if (a.links || a.forced) launch_sweep_mode<S, STREAM_AB, true>(a, resid, s);

@@ -57,6 +57,7 @@ struct SweepArgs {
   void* dst_pop[19];        // so that each access is one add and one wide multiply-add)
   uint32_t nx, ny, nz, N;
   FastDiv div_nx, div_ny;
+  FastDiv div_nxh;    // nx / 2 (the paired binary16 sweep, even nx)
   uint32_t periodic;  // bit a set: axis a is periodic
   uint32_t pressure;  // bit f set: face f is a pressure face
   double rho0;

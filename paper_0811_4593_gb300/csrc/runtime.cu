@@ -369,6 +369,7 @@ lbm_status lbm_create_scheme(int nx, int ny, int nz, double tau, const lbm_face_
   a.nx = nx; a.ny = ny; a.nz = nz; a.N = ctx->N;
   a.div_nx = lbm::make_fastdiv(uint32_t(nx));
   a.div_ny = lbm::make_fastdiv(uint32_t(ny));
+  a.div_nxh = lbm::make_fastdiv(uint32_t(nx / 2 > 0 ? nx / 2 : 1));
   a.periodic = 0;
   for (int ax = 0; ax < 3; ++ax)
     if (faces[2 * ax].kind == LBM_FACE_PERIODIC) a.periodic |= 1u << ax;
