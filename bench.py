@@ -555,6 +555,162 @@ def study_duct(args):
                       "rho_in_out": [1.002, 0.998], "rows": rows, "paper_slope": 2}), flush=True)
 
 
+def _gpu_study_setup():
+    import torch
+
+    from paper_0811_4593_gb300 import build as lib_build
+    lib_build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def study_poiseuille(args):
+    """Plane Poiseuille sweep (4 x 4 x Lz, Lz = 16 .. 256, tau 0.55 / 1 / 1.5, peak
+    0.02): the prescribed parabola at inlet and outlet is an exact steady solution of
+    the method. Per case: FP64 steps until the residual falls below 1e-10; the FP64
+    oracle run for the same steps; FP32 and binary16 runs of the same length. Reported:
+    L2 error against the parabola, maximum velocity difference to the oracle, the
+    residual reached, or the step at which a run diverged."""
+    import numpy as np
+
+    import oracle
+    import paper_0811_4593_gb300 as lbm
+    _gpu_study_setup()
+    rows = []
+    for tau in (0.55, 1.0, 1.5):
+        for lz in (16, 32, 64, 128, 256):
+            wl = inp.poiseuille(lz, tau, 0.02)
+            exact = 0.02 * inp.parabola(lz)[:, None, None] * np.ones((1, wl.ny, wl.nx))
+            row = {"tau": tau, "lz": lz}
+            steps = None
+            for prec in ("f64", "f32", "f16"):
+                if prec != "f64" and steps is None:
+                    row[prec] = {"skipped": "the FP64 run diverged"}
+                    continue
+                t0 = time.perf_counter()
+                res = None
+                with lbm.Lattice.from_workload(wl, prec) as lat:
+                    try:
+                        done = 0
+                        if prec == "f64":
+                            while done < 400_000:
+                                r, _ = lat.step_residual(100)
+                                done += 100
+                                if r < 1e-10:
+                                    break
+                            steps = done
+                        else:
+                            while done < steps:
+                                r, _ = lat.step_residual(min(100, steps - done))
+                                done += min(100, steps - done)
+                        res = r
+                        _, u = lat.macros()
+                        u = u.double().cpu().numpy()
+                    except lbm.LBMDiverged:
+                        row[prec] = {"diverged_at_step": lat.info()["steps"]}
+                        if prec == "f64":
+                            steps = None
+                        continue
+                l2 = float(np.sqrt(((u[0] - exact) ** 2).sum() / (exact ** 2).sum()))
+                row[prec] = {"l2_vs_parabola": l2, "residual": res, "steps": done,
+                             "max_transverse": float(np.abs(u[1:]).max()), "seconds": round(time.perf_counter() - t0, 2)}
+                if prec == "f64":
+                    olat = oracle.Lattice.from_workload(wl)
+                    f = oracle.run(olat, oracle.init_equilibrium(olat), steps)
+                    _, uo = oracle.macros(olat, f)
+                    row["oracle_u"] = uo
+                if "oracle_u" in row:
+                    row[prec]["max_vs_oracle"] = float(np.abs(u - row["oracle_u"]).max() / 0.02)
+            row.pop("oracle_u", None)
+            rows.append(row)
+    print(json.dumps({"study": "plane Poiseuille sweep (Sec. Numerical Results)", "rows": rows}), flush=True)
+
+
+def study_duct_config(args):
+    """The 256 x 64 x 64 duct (inlet and outlet product parabola, peak 0.05 at 30
+    degrees, resting walls), 20000 steps at tau 0.6 and 1.0 in FP64 and FP32 on the GPU
+    against the FP64 oracle run on the host cores; the mid-duct axial velocity against
+    eq. squarechannel at matched flux."""
+    import numpy as np
+
+    import oracle
+    import paper_0811_4593_gb300 as lbm
+    _gpu_study_setup()
+
+    def series(ny, nz, terms=50):
+        b = ny - 1.0
+        ys = np.arange(ny) - (ny - 1) / 2.0
+        zs = np.arange(nz) - (nz - 1) / 2.0
+        Z, Y = np.meshgrid(zs, ys, indexing="ij")
+        C = np.zeros_like(Y)
+        for m in range(terms):
+            k = 2 * m + 1
+            C += (-1) ** m * np.cosh(k * np.pi * Z / b) * np.cos(k * np.pi * Y / b) / (k ** 3 * np.cosh(k * np.pi / 2))
+        return b * b / 4 - Y ** 2 - C * 8 * b * b / np.pi ** 3
+
+    steps = int(getattr(args, "study_steps", 0) or 20000)
+    out = {"study": f"duct 256x64x64, {steps} steps", "rows": []}
+    for tau in (0.6, 1.0):
+        wl = inp.duct(256, 64, 64, tau, 0.05, 30.0)
+        t0 = time.perf_counter()
+        olat = oracle.Lattice.from_workload(wl)
+        ref = oracle.run(olat, oracle.init_equilibrium(olat), steps)
+        _, uo = oracle.macros(olat, ref)
+        row = {"tau": tau, "oracle_seconds": round(time.perf_counter() - t0, 1), "oracle_threads": oracle.threads()}
+        scale = np.abs(uo).max()
+        for prec in ("f64", "f32"):
+            t0 = time.perf_counter()
+            with lbm.Lattice.from_workload(wl, prec) as lat:
+                lat.step(steps)
+                _, u = lat.macros()
+                u = u.double().cpu().numpy()
+            row[prec] = {"max_vs_oracle": float(np.abs(u - uo).max() / scale),
+                         "seconds": round(time.perf_counter() - t0, 2)}
+        mid = uo[:, :, :, wl.nx // 2]                       # [3][z][y]
+        axial = mid[0] * math.cos(math.radians(30)) + mid[1] * math.sin(math.radians(30))
+        shape = series(wl.ny, wl.nz)
+        an = shape * (axial.sum() / shape.sum())           # matched flux
+        row["mid_duct_l2_vs_squarechannel"] = float(np.sqrt(((axial - an) ** 2).sum() / (an ** 2).sum()))
+        out["rows"].append(row)
+    print(json.dumps(out), flush=True)
+
+
+def study_force(args):
+    """The paper's body-force check: 32^3, walls on the x faces, periodic y and z, tau 2
+    and 1: maximum deviation of the velocity after the boundary rule from eq. poiseuille
+    (viscosity from eq. visc) and the velocity on the wall nodes, on the GPU in FP64 and
+    FP32; the same with the transverse corrections set to zero (FP64 oracle)."""
+    import numpy as np
+
+    import oracle
+    import paper_0811_4593_gb300 as lbm
+    _gpu_study_setup()
+    rows = []
+    for tau, steps in ((2.0, 8000), (1.0, 22000)):
+        wl = inp.force_poiseuille(n=32, tau=tau, force=1e-6, wall_axis=0, flow_axis=2, other=None)
+        F = wl.force[2]
+        x = np.arange(wl.nx)
+        h = (wl.nx - 1) / 2.0
+        row = {"tau": tau, "steps": steps, "force": F}
+        for prec in ("f64", "f32", "oracle_n_zero"):
+            if prec == "oracle_n_zero":
+                olat = oracle.Lattice.from_workload(wl)
+                f = oracle.run(olat, oracle.init_equilibrium(olat), steps, form=oracle.FORM_COMPACT_NO_N)
+                rho, u = oracle.macros(olat, f)
+            else:
+                with lbm.Lattice.from_workload(wl, prec) as lat:
+                    lat.step(steps)
+                    rho, u = lat.macros()
+                    rho, u = rho.double().cpu().numpy(), u.double().cpu().numpy()
+            u_pre = u[2] - F / rho
+            exact = F / (2.0 * rho * (tau - 0.5) / 3.0) * (h * h - (x - h) ** 2)
+            row[prec] = {"max_rel_error": float(np.abs(u_pre - exact).max() / exact.max()),
+                         "wall_velocity": float(np.abs(u_pre[:, :, [0, -1]]).max()),
+                         "u_max": float(exact.max())}
+        rows.append(row)
+    print(json.dumps({"study": "body-force Poiseuille 32^3 (eq. gravity, eq. poiseuille)", "rows": rows}),
+          flush=True)
+
+
 def reference(args):
     """The FP64 oracle on the host cores, `--steps` timed steps after `--warmup` on the
     bounded sample of the workload; rank 0 only."""
@@ -597,7 +753,9 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true", help="run the serving mix instead of the sweep benchmark")
-    ap.add_argument("--study", choices=["tilted", "duct"], help="run a reproduction study instead of the benchmark")
+    ap.add_argument("--study", choices=["tilted", "duct", "poiseuille", "duct-config", "force"],
+                    help="run a reproduction study instead of the benchmark")
+    ap.add_argument("--study-steps", type=int, default=0, help="steps of the duct-config study (default 20000)")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--capacity-requests", type=int, default=200)
     ap.add_argument("--slots", type=int, default=512)
@@ -614,6 +772,12 @@ def main():
         study_tilted(args)
     elif args.study == "duct":
         study_duct(args)
+    elif args.study == "poiseuille":
+        study_poiseuille(args)
+    elif args.study == "duct-config":
+        study_duct_config(args)
+    elif args.study == "force":
+        study_force(args)
     elif args.serving:
         serving(args)
     else:
