@@ -29,6 +29,19 @@ __device__ __forceinline__ void static_for(F&& f) {
 template <typename S> struct ComputeOf { using T = float; };
 template <> struct ComputeOf<double> { using T = double; };
 
+// Arithmetic with one explicit rounding per operation. The compiler may neither fuse
+// nor reorder these, so every sweep variant (single node, paired, residual, batched,
+// AA, geometry) computes the same bits for a node; a plain a * b + c may be fused in one
+// kernel and not in another.
+__device__ __forceinline__ float op_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double op_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float op_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double op_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float op_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double op_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float op_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double op_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Storage codec: stored value <-> register value v (h_i for shifted storage, f_i for
 // FP64) in the compute type.
 template <typename S> struct Storage;
@@ -113,23 +126,26 @@ __device__ __forceinline__ void fill_unknowns(T (&h)[Q], T rho, const T (&u)[3])
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     if constexpr (ca(k, A) == 0) {
-      if constexpr (ca(k, B) != 0) sb += T(ca(k, B)) * h[k];
-      if constexpr (ca(k, C) != 0) sc += T(ca(k, C)) * h[k];
+      if constexpr (ca(k, B) != 0) sb = ca(k, B) > 0 ? op_add(sb, h[k]) : op_sub(sb, h[k]);
+      if constexpr (ca(k, C) != 0) sc = ca(k, C) > 0 ? op_add(sc, h[k]) : op_sub(sc, h[k]);
     }
   });
   const T third = T(1) / T(3);
-  const T NB = T(0.5) * sb - rho * u[B] * third;
-  const T NC = T(0.5) * sc - rho * u[C] * third;
+  const T NB = op_sub(op_mul(T(0.5), sb), op_mul(op_mul(rho, u[B]), third));
+  const T NC = op_sub(op_mul(T(0.5), sc), op_mul(op_mul(rho, u[C]), third));
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     if constexpr (SG * ca(k, A) > 0) {
       constexpr int m = opp(k);
-      const T cu = T(cx(k)) * u[0] + T(cy(k)) * u[1] + T(cz(k)) * u[2];
+      T cu = T(0);
+      if constexpr (cx(k) != 0) cu = cx(k) > 0 ? op_add(cu, u[0]) : op_sub(cu, u[0]);
+      if constexpr (cy(k) != 0) cu = cy(k) > 0 ? op_add(cu, u[1]) : op_sub(cu, u[1]);
+      if constexpr (cz(k) != 0) cu = cz(k) > 0 ? op_add(cu, u[2]) : op_sub(cu, u[2]);
       const T coef = T(6 * w36(k)) / T(36);
       T t = T(0);
-      if constexpr (ca(k, B) != 0) t += T(ca(k, B)) * NB;
-      if constexpr (ca(k, C) != 0) t += T(ca(k, C)) * NC;
-      h[k] = h[m] + coef * rho * cu - t;
+      if constexpr (ca(k, B) != 0) t = ca(k, B) > 0 ? op_add(t, NB) : op_sub(t, NB);
+      if constexpr (ca(k, C) != 0) t = ca(k, C) > 0 ? op_add(t, NC) : op_sub(t, NC);
+      h[k] = op_sub(op_fma(op_mul(coef, rho), cu, h[m]), t);
     }
   });
 }
@@ -477,24 +493,24 @@ __device__ __forceinline__ Moments<T> moments(const T (&h)[Q], T rho0) {
   T sp = T(0), sm = T(0), s0 = T(0), jy = T(0), jz = T(0);
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    if constexpr (cx(k) > 0) sp += h[k];
-    else if constexpr (cx(k) < 0) sm += h[k];
-    else s0 += h[k];
-    if constexpr (cy(k) > 0) jy += h[k];
-    else if constexpr (cy(k) < 0) jy -= h[k];
-    if constexpr (cz(k) > 0) jz += h[k];
-    else if constexpr (cz(k) < 0) jz -= h[k];
+    if constexpr (cx(k) > 0) sp = op_add(sp, h[k]);
+    else if constexpr (cx(k) < 0) sm = op_add(sm, h[k]);
+    else s0 = op_add(s0, h[k]);
+    if constexpr (cy(k) > 0) jy = op_add(jy, h[k]);
+    else if constexpr (cy(k) < 0) jy = op_sub(jy, h[k]);
+    if constexpr (cz(k) > 0) jz = op_add(jz, h[k]);
+    else if constexpr (cz(k) < 0) jz = op_sub(jz, h[k]);
   });
   Moments<T> m;
-  m.drho = (sp + sm) + s0;
-  m.rho = rho0 + m.drho;
-  m.jx = sp - sm;
+  m.drho = op_add(op_add(sp, sm), s0);
+  m.rho = op_add(rho0, m.drho);
+  m.jx = op_sub(sp, sm);
   m.jy = jy;
   m.jz = jz;
   const T inv = T(1) / m.rho;
-  m.ux = m.jx * inv;
-  m.uy = jy * inv;
-  m.uz = jz * inv;
+  m.ux = op_mul(m.jx, inv);
+  m.uy = op_mul(jy, inv);
+  m.uz = op_mul(jz, inv);
   return m;
 }
 
@@ -508,27 +524,31 @@ __device__ __forceinline__ Moments<T> moments(const T (&h)[Q], T rho0) {
 // multiply-add, two additions and two fused relaxations.
 template <typename T>
 __device__ __forceinline__ void collide(T (&h)[Q], const Moments<T>& m, T omega) {
-  const T b = m.drho - T(1.5) * (m.jx * m.ux + m.jy * m.uy + m.jz * m.uz);
-  const T keep = T(1) - omega;
-  const T ow_axis = omega * wgt<T>(0), ow_diag = omega * wgt<T>(6);
-  const T ob_axis = ow_axis * b, ob_diag = ow_diag * b;
-  const T g_axis = T(4.5) * ow_axis, g_diag = T(4.5) * ow_diag;
-  const T a_axis = T(3) * ow_axis, a_diag = T(3) * ow_diag;
+  const T ju = op_fma(m.jz, m.uz, op_fma(m.jy, m.uy, op_mul(m.jx, m.ux)));
+  const T b = op_fma(T(-1.5), ju, m.drho);
+  const T keep = op_sub(T(1), omega);
+  const T ow_axis = op_mul(omega, wgt<T>(0)), ow_diag = op_mul(omega, wgt<T>(6));
+  const T ob_axis = op_mul(ow_axis, b), ob_diag = op_mul(ow_diag, b);
+  const T g_axis = op_mul(T(4.5), ow_axis), g_diag = op_mul(T(4.5), ow_diag);
+  const T a_axis = op_mul(T(3), ow_axis), a_diag = op_mul(T(3), ow_diag);
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     constexpr int o = opp(k);
     if constexpr (k == Q - 1) {
-      h[k] = keep * h[k] + (omega * wgt<T>(k)) * b;
+      h[k] = op_fma(keep, h[k], op_mul(op_mul(omega, wgt<T>(k)), b));
     } else if constexpr (k < o) {
       constexpr bool axis = w36(k) == 2;
       T cj = T(0), cu = T(0);
-      if constexpr (cx(k) != 0) { cj += T(cx(k)) * m.jx; cu += T(cx(k)) * m.ux; }
-      if constexpr (cy(k) != 0) { cj += T(cy(k)) * m.jy; cu += T(cy(k)) * m.uy; }
-      if constexpr (cz(k) != 0) { cj += T(cz(k)) * m.jz; cu += T(cz(k)) * m.uz; }
-      const T t = (axis ? g_axis : g_diag) * cj * cu + (axis ? ob_axis : ob_diag);
-      const T a = (axis ? a_axis : a_diag) * cj;
-      h[k] = keep * h[k] + (t + a);
-      h[o] = keep * h[o] + (t - a);
+      if constexpr (cx(k) != 0) { cj = cx(k) > 0 ? op_add(cj, m.jx) : op_sub(cj, m.jx);
+                                  cu = cx(k) > 0 ? op_add(cu, m.ux) : op_sub(cu, m.ux); }
+      if constexpr (cy(k) != 0) { cj = cy(k) > 0 ? op_add(cj, m.jy) : op_sub(cj, m.jy);
+                                  cu = cy(k) > 0 ? op_add(cu, m.uy) : op_sub(cu, m.uy); }
+      if constexpr (cz(k) != 0) { cj = cz(k) > 0 ? op_add(cj, m.jz) : op_sub(cj, m.jz);
+                                  cu = cz(k) > 0 ? op_add(cu, m.uz) : op_sub(cu, m.uz); }
+      const T t = op_fma(op_mul(axis ? g_axis : g_diag, cj), cu, axis ? ob_axis : ob_diag);
+      const T a = op_mul(axis ? a_axis : a_diag, cj);
+      h[k] = op_fma(keep, h[k], op_add(t, a));
+      h[o] = op_fma(keep, h[o], op_sub(t, a));
     }
   });
 }
@@ -584,8 +604,9 @@ __device__ __forceinline__ void residual_terms(const Moments<T>& m, double rho0,
   snap[N + cell] = m.uy;
   snap[2ull * N + cell] = m.uz;
   v[0] = rho;
-  v[1] = (u[0] - p[0]) * (u[0] - p[0]) + (u[1] - p[1]) * (u[1] - p[1]) + (u[2] - p[2]) * (u[2] - p[2]);
-  v[2] = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const double d0 = op_sub(u[0], p[0]), d1 = op_sub(u[1], p[1]), d2 = op_sub(u[2], p[2]);
+  v[1] = op_fma(d2, d2, op_fma(d1, d1, op_mul(d0, d0)));
+  v[2] = op_fma(u[2], u[2], op_fma(u[1], u[1], op_mul(u[0], u[0])));
   const bool ok = isfinite(rho) && rho > 0.0 && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
   v[3] = ok ? 0.0 : 1.0;
 }
