@@ -287,7 +287,7 @@ def _sample_nodes(nx, ny, nz, planes, seed=5):
     return np.array(sorted({(z * ny + y) * nx + x for x, y, z in nodes}), np.int64)
 
 
-@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
 def test_full_size_channel_one_step_sampled(prec):
     import oracle
     import paper_0811_4593_gb300 as lbm
@@ -308,7 +308,7 @@ def test_full_size_channel_one_step_sampled(prec):
     y = (nodes // nx) % ny
     z = nodes // (nx * ny)
     g = np.stack([got[int(zz)][:, yy, xx] for xx, yy, zz in zip(x, y, z)])
-    tol = 2e-6 if prec == "f32" else 2e-5
+    tol = {"f64": 1e-13, "f32": 2e-6, "f16": 2e-5}[prec]
     assert np.abs(g - ref).max() < tol, np.abs(g - ref).max()
 
 
