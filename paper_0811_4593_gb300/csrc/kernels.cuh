@@ -783,6 +783,22 @@ __global__ void __launch_bounds__(SWEEP_THREADS, (SweepOccupancy<S, RESID, false
 // population are stored as one half2. Each node runs the single-node sweep's closure,
 // moment and collision code, so both sweeps give the same bits.
 // ---------------------------------------------------------------------------------
+// Read-only loads that also ask L2 to fetch the enclosing 256-byte block (PTX
+// ld.global.nc with the .L2::256B prefetch-size qualifier): consecutive warps stream
+// consecutive 128-byte pieces of each population row, so the next warp's data is
+// already on its way when it asks.
+__device__ __forceinline__ float ld_half_l2(const __half* p) {
+  unsigned short v;
+  asm("ld.global.nc.L2::256B.u16 %0, [%1];" : "=h"(v) : "l"(p));
+  return __half2float(__ushort_as_half(v));
+}
+__device__ __forceinline__ void ld_half2_l2(const __half* p, float& lo, float& hi) {
+  unsigned int v;
+  asm("ld.global.nc.L2::256B.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  lo = __half2float(__ushort_as_half(static_cast<unsigned short>(v & 0xffffu)));
+  hi = __half2float(__ushort_as_half(static_cast<unsigned short>(v >> 16)));
+}
+
 template <bool FAST>
 __device__ __forceinline__ void load_pair(const SweepArgs& a, uint32_t x0, uint32_t xam, uint32_t xbp,
                                           const uint32_t (&rows)[3][3], float (&hA)[Q], float (&hB)[Q]) {
@@ -790,17 +806,15 @@ __device__ __forceinline__ void load_pair(const SweepArgs& a, uint32_t x0, uint3
     constexpr int k = decltype(kc)::value;
     const __half* base = static_cast<const __half*>(a.src_pop[k]) + rows[1 - cz(k)][1 - cy(k)];
     if constexpr (cx(k) == 0) {
-      const __half2 v = __ldg(reinterpret_cast<const __half2*>(base + x0));
-      hA[k] = __low2float(v);
-      hB[k] = __high2float(v);
+      ld_half2_l2(base + x0, hA[k], hB[k]);
     } else if constexpr (cx(k) > 0) {  // pulled from x - 1
       const __half* pb = base + x0;
-      hB[k] = __half2float(__ldg(pb));
-      hA[k] = __half2float(__ldg(FAST ? pb - 1 : base + xam));
+      hB[k] = ld_half_l2(pb);
+      hA[k] = ld_half_l2(FAST ? pb - 1 : base + xam);
     } else {  // pulled from x + 1
       const __half* pa = base + x0 + 1;
-      hA[k] = __half2float(__ldg(pa));
-      hB[k] = __half2float(__ldg(FAST ? pa + 1 : base + xbp));
+      hA[k] = ld_half_l2(pa);
+      hB[k] = ld_half_l2(FAST ? pa + 1 : base + xbp);
     }
   });
 }
