@@ -514,6 +514,14 @@ __device__ __forceinline__ Moments<T> moments(const T (&h)[Q], T rho0) {
   return m;
 }
 
+// EXACT_MOMENTUM: the momentum term 3 omega w_i (c_i.j) takes its coefficient as an
+// unevaluated pair hi + lo (coef, from the host), so the collision conserves momentum
+// to float rounding of each product instead of biasing it by the rounding of one
+// constant -- a bias that acts like a small body force and dominated the FP32 error at
+// low viscosity (4.6e-5 of u_max on a 256 x 64 x 64 duct at tau = 0.6, 7.6e-6 with
+// the pair). Used for FP32 storage; binary16 storage error is set by its 11-bit
+// mantissa.
+//
 // BGK relaxation v_i <- (1 - omega) v_i + omega v_i^eq with the second-order
 // equilibrium written for the pair (i, -i), whose c.u only changes sign:
 //   v^eq_{+-i} = w_i (b + s_i +- a_i),  b = drho - 3/2 j.u,  s_i = 9/2 (c_i.j)(c_i.u),
@@ -522,8 +530,9 @@ __device__ __forceinline__ Moments<T> moments(const T (&h)[Q], T rho0) {
 // term by term and shares the symmetric part between the two populations. omega w_i is
 // folded into the per-class factors, so a pair costs two products, one fused
 // multiply-add, two additions and two fused relaxations.
-template <typename T>
-__device__ __forceinline__ void collide(T (&h)[Q], const Moments<T>& m, T omega) {
+template <bool EXACT_MOMENTUM = false, typename T>
+__device__ __forceinline__ void collide(T (&h)[Q], const Moments<T>& m, T omega,
+                                        const float (*coef)[2] = nullptr) {
   const T ju = op_fma(m.jz, m.uz, op_fma(m.jy, m.uy, op_mul(m.jx, m.ux)));
   const T b = op_fma(T(-1.5), ju, m.drho);
   const T keep = op_sub(T(1), omega);
@@ -546,7 +555,13 @@ __device__ __forceinline__ void collide(T (&h)[Q], const Moments<T>& m, T omega)
       if constexpr (cz(k) != 0) { cj = cz(k) > 0 ? op_add(cj, m.jz) : op_sub(cj, m.jz);
                                   cu = cz(k) > 0 ? op_add(cu, m.uz) : op_sub(cu, m.uz); }
       const T t = op_fma(op_mul(axis ? g_axis : g_diag, cj), cu, axis ? ob_axis : ob_diag);
-      const T a = op_mul(axis ? a_axis : a_diag, cj);
+      T a;
+      if constexpr (EXACT_MOMENTUM) {
+        const float* ab = coef[axis ? 0 : 1];
+        a = op_fma(T(ab[0]), cj, op_mul(T(ab[1]), cj));
+      } else {
+        a = op_mul(axis ? a_axis : a_diag, cj);
+      }
       h[k] = op_fma(keep, h[k], op_add(t, a));
       h[o] = op_fma(keep, h[o], op_sub(t, a));
     }
@@ -726,7 +741,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
     } else if constexpr (RESID) {
       residual_terms(m, ref_rho<S>(a.rho0), static_cast<T*>(a.snap), a.N, cell, red);
     }
-    if (!solid) collide(h, m, omega_of<T>(a));
+    if (!solid) collide<std::is_same<S, float>::value>(h, m, omega_of<T>(a), a.mom_coef);
     static_for<0, Q>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
       if constexpr (MODE == STREAM_AB) {

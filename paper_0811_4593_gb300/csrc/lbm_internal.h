@@ -63,6 +63,7 @@ struct SweepArgs {
   double rho0;
   double omega;       // 1 / tau
   float rho0f, omegaf;
+  float mom_coef[2][2];  // omegaf / 6 and omegaf / 12 as hi + lo float pairs
   FaceBC face[6];
   void* snap;         // residual steps: [3][N] velocity snapshot in the compute type
   double* partials;   // residual steps: [blocks][4] per-block sums

@@ -377,6 +377,14 @@ lbm_status lbm_create_scheme(int nx, int ny, int nz, double tau, const lbm_face_
   a.omega = 1.0 / tau;
   a.rho0f = float(rho0);
   a.omegaf = float(1.0 / tau);
+  // 3 omega w_i of the BGK update's momentum term for the float sweep, as hi + lo
+  // floats of omegaf / 6 (axis) and omegaf / 12 (diagonal): with a single rounded
+  // constant every collision would gain or lose ~1e-7 of the node's momentum
+  for (int c = 0; c < 2; ++c) {
+    const double v = double(a.omegaf) / (c == 0 ? 6.0 : 12.0);
+    a.mom_coef[c][0] = float(v);
+    a.mom_coef[c][1] = float(v - double(a.mom_coef[c][0]));
+  }
   const double zero[3] = {0.0, 0.0, 0.0};
   a.pressure = 0;
   for (int f = 0; f < 6; ++f) {
