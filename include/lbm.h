@@ -215,6 +215,12 @@ LBM_API lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* solid, const in
  * only; not while attached to a batch (LBM_ERR_STATE). Takes effect with the next step. */
 LBM_API lbm_status lbm_set_body_force(lbm_ctx* ctx, const double force[3]);
 
+/* Every device buffer of a context lies between two 256-byte guard regions filled with
+ * a fixed pattern at allocation (device_bytes counts the buffers, not the guards). This
+ * reads the guards back and returns LBM_ERR_STATE, naming the buffer, if any byte
+ * changed -- evidence of a write outside a buffer. Synchronises. */
+LBM_API lbm_status lbm_check_guards(lbm_ctx* ctx);
+
 /* Block the host until the context's stream is idle; reports asynchronous errors. */
 LBM_API lbm_status lbm_sync(lbm_ctx* ctx);
 

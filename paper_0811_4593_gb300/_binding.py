@@ -42,6 +42,7 @@ EXPORTS = {
     "lbm_set_solid": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_set_geometry": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_set_body_force": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "lbm_check_guards": (C.c_int, [C.c_void_p]),
     "lbm_info": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_batch_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
@@ -279,11 +280,19 @@ class Lattice:
             lat.set_body_force(wl.force)
         return lat
 
+    def check_guards(self):
+        """Raise LBMError if a write landed just outside one of the lattice's buffers."""
+        check(lib().lbm_check_guards(self.ctx), self.ctx)
+
     # -- lifetime -------------------------------------------------------------------
     def close(self):
         if getattr(self, "_ctx", None):
-            lib().lbm_destroy(self._ctx)
-            self._ctx = None
+            ctx, self._ctx = self._ctx, None
+            try:
+                if os.environ.get("LBM_CHECK_GUARDS") == "1":
+                    check(lib().lbm_check_guards(ctx), ctx)
+            finally:
+                lib().lbm_destroy(ctx)
 
     def __del__(self):
         try:

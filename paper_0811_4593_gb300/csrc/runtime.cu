@@ -23,9 +23,15 @@ void* g_user = nullptr;
 thread_local std::string g_err = "no error";
 
 struct Allocation {
-  void* ptr;
-  size_t bytes;
+  void* ptr;     // start of the allocation (the leading guard)
+  size_t bytes;  // bytes handed out, between the two guards
 };
+
+// Every context buffer sits between two guard regions filled with GUARD_BYTE when it is
+// allocated; lbm_check_guards reads them back, so a write just outside a buffer (the
+// kind an index error makes) is caught without a device-side sanitizer.
+constexpr size_t GUARD = 256;
+constexpr unsigned char GUARD_BYTE = 0xa5;
 
 }  // namespace
 
@@ -130,17 +136,25 @@ struct DeviceGuard {
 
 void* ctx_alloc(lbm_ctx* ctx, size_t bytes) {
   void* p = nullptr;
+  const size_t total = bytes + 2 * GUARD;
   if (ctx->alloc) {
-    p = ctx->alloc(bytes, ctx->user);
-  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = ctx->alloc(total, ctx->user);
+  } else if (cudaMalloc(&p, total) != cudaSuccess) {
     cudaGetLastError();
     p = nullptr;
   }
-  if (p) {
-    ctx->allocations.push_back({p, bytes});
-    ctx->device_bytes += int64_t(bytes);
+  if (!p) return nullptr;
+  char* base = static_cast<char*>(p);
+  if (cudaMemset(base, GUARD_BYTE, GUARD) != cudaSuccess ||
+      cudaMemset(base + GUARD + bytes, GUARD_BYTE, GUARD) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->release) ctx->release(p, ctx->user);
+    else cudaFree(p);
+    return nullptr;
   }
-  return p;
+  ctx->allocations.push_back({p, bytes});
+  ctx->device_bytes += int64_t(bytes);
+  return base + GUARD;
 }
 
 void ctx_free_all(lbm_ctx* ctx) {
@@ -690,6 +704,27 @@ lbm_status lbm_set_body_force(lbm_ctx* ctx, const double force[3]) {
     a.tforcef[i] = float(a.tforce[i]);
   }
   a.forced = (force[0] != 0.0 || force[1] != 0.0 || force[2] != 0.0) ? 1u : 0u;
+  return LBM_OK;
+}
+
+lbm_status lbm_check_guards(lbm_ctx* ctx) {
+  if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, LBM_ERR_CUDA, "cannot make device %d current", ctx->device);
+  if (lbm_status st0 = settle(ctx); st0 != LBM_OK) return st0;
+  LBM_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "synchronising");
+  std::vector<unsigned char> h(2 * GUARD);
+  for (size_t i = 0; i < ctx->allocations.size(); ++i) {
+    const Allocation& a = ctx->allocations[i];
+    const char* base = static_cast<const char*>(a.ptr);
+    LBM_CUDA(ctx, cudaMemcpy(h.data(), base, GUARD, cudaMemcpyDeviceToHost), "reading a guard");
+    LBM_CUDA(ctx, cudaMemcpy(h.data() + GUARD, base + GUARD + a.bytes, GUARD, cudaMemcpyDeviceToHost),
+             "reading a guard");
+    for (size_t j = 0; j < 2 * GUARD; ++j)
+      if (h[j] != GUARD_BYTE)
+        return fail(ctx, LBM_ERR_STATE, "buffer %zu (%zu bytes): guard %s it overwritten at byte %zu", i, a.bytes,
+                    j < GUARD ? "below" : "above", j < GUARD ? j : j - GUARD);
+  }
   return LBM_OK;
 }
 

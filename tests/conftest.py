@@ -12,6 +12,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# every lattice a GPU test closes first has the guard regions around its device buffers
+# checked (a write just outside a buffer fails the test that made it)
+os.environ.setdefault("LBM_CHECK_GUARDS", "1")
+
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the compiled CUDA library")

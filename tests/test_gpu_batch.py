@@ -177,3 +177,27 @@ def test_attach_rules():
         assert b.info()["attached"] == 0
         b.step(2)                                        # empty batch: no-op
         c.close()
+
+
+def test_injected_nan_is_reported_per_lattice():
+    # a host-built state with one non-finite population: the next residual step reports
+    # the lattice as diverged, alone and in a batch, without touching its neighbours
+    import paper_0811_4593_gb300 as lbm
+    wl = inp.duct(20, 9, 9, 0.9, 0.05, 30.0)
+    bad_state = encode(noisy_state((19, wl.nz, wl.ny, wl.nx), 5), "f32")
+    bad_state[3, 4, 4, 10] = np.nan
+    with start(wl, "f32", 5) as lat:
+        lat.set_populations(bad_state)
+        with pytest.raises(lbm.LBMDiverged):
+            lat.step_residual(1)
+    with lbm.Batch(3, "f32") as b:
+        good = start(wl, "f32", 6)
+        bad = start(wl, "f32", 7)
+        bad.set_populations(bad_state)
+        b.attach(0, good)
+        b.attach(2, bad)
+        b.step(1, residual=True)
+        status = [s for _, _, s in b.results()]
+        assert status == [0, 1, -4]
+        good.close()
+        bad.close()
