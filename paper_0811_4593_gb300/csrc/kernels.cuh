@@ -42,6 +42,46 @@ __device__ __forceinline__ double op_mul(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float op_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double op_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// Signed sums whose first term is taken as it is (negation is exact), so that no
+// rounded addition of zero is ever issued.
+template <int SGN, typename T>
+__device__ __forceinline__ T sgn(T v) { return SGN > 0 ? v : -v; }
+template <int SGN, typename T>
+__device__ __forceinline__ void acc(T& s, T v, bool first) {
+  if (first) s = sgn<SGN>(v);
+  else s = SGN > 0 ? op_add(s, v) : op_sub(s, v);
+}
+// c_k . (x, y, z) for a moving population k
+template <int k, typename T>
+__device__ __forceinline__ T dot_c(T x, T y, T z) {
+  constexpr int X = cx(k), Y = cy(k), Z = cz(k);
+  T s = T(0);
+  if constexpr (X != 0) acc<X>(s, x, true);
+  if constexpr (Y != 0) acc<Y>(s, y, X == 0);
+  if constexpr (Z != 0) acc<Z>(s, z, X == 0 && Y == 0);
+  return s;
+}
+// first population index lying in the plane normal to axis A with component X != 0
+template <int A>
+__host__ __device__ constexpr int first_in_plane(int X) {
+  for (int k = 0; k < Q; ++k)
+    if (ca(k, A) == 0 && ca(k, X) != 0) return k;
+  return -1;
+}
+// first population index with component a of sign `sg` (0: component zero)
+__host__ __device__ constexpr int first_with(int a, int sg) {
+  for (int k = 0; k < Q; ++k) {
+    const int c = ca(k, a);
+    if ((sg > 0 && c > 0) || (sg < 0 && c < 0) || (sg == 0 && c == 0)) return k;
+  }
+  return -1;
+}
+__host__ __device__ constexpr int first_nonzero(int a) {
+  for (int k = 0; k < Q; ++k)
+    if (ca(k, a) != 0) return k;
+  return -1;
+}
+
 // Storage codec: stored value <-> register value v (h_i for shifted storage, f_i for
 // FP64) in the compute type.
 template <typename S> struct Storage;
@@ -126,8 +166,8 @@ __device__ __forceinline__ void fill_unknowns(T (&h)[Q], T rho, const T (&u)[3])
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     if constexpr (ca(k, A) == 0) {
-      if constexpr (ca(k, B) != 0) sb = ca(k, B) > 0 ? op_add(sb, h[k]) : op_sub(sb, h[k]);
-      if constexpr (ca(k, C) != 0) sc = ca(k, C) > 0 ? op_add(sc, h[k]) : op_sub(sc, h[k]);
+      if constexpr (ca(k, B) != 0) acc<ca(k, B)>(sb, h[k], k == first_in_plane<A>(B));
+      if constexpr (ca(k, C) != 0) acc<ca(k, C)>(sc, h[k], k == first_in_plane<A>(C));
     }
   });
   const T third = T(1) / T(3);
@@ -137,15 +177,22 @@ __device__ __forceinline__ void fill_unknowns(T (&h)[Q], T rho, const T (&u)[3])
     constexpr int k = decltype(kc)::value;
     if constexpr (SG * ca(k, A) > 0) {
       constexpr int m = opp(k);
-      T cu = T(0);
-      if constexpr (cx(k) != 0) cu = cx(k) > 0 ? op_add(cu, u[0]) : op_sub(cu, u[0]);
-      if constexpr (cy(k) != 0) cu = cy(k) > 0 ? op_add(cu, u[1]) : op_sub(cu, u[1]);
-      if constexpr (cz(k) != 0) cu = cz(k) > 0 ? op_add(cu, u[2]) : op_sub(cu, u[2]);
+      const T cu = dot_c<k>(u[0], u[1], u[2]);
       const T coef = T(6 * w36(k)) / T(36);
-      T t = T(0);
-      if constexpr (ca(k, B) != 0) t = ca(k, B) > 0 ? op_add(t, NB) : op_sub(t, NB);
-      if constexpr (ca(k, C) != 0) t = ca(k, C) > 0 ? op_add(t, NC) : op_sub(t, NC);
-      h[k] = op_sub(op_fma(op_mul(coef, rho), cu, h[m]), t);
+      const T hk = op_fma(op_mul(coef, rho), cu, h[m]);
+      // minus the transverse correction t_i.N
+      if constexpr (ca(k, B) != 0 && ca(k, C) != 0) {
+        T t = T(0);
+        acc<ca(k, B)>(t, NB, true);
+        acc<ca(k, C)>(t, NC, false);
+        h[k] = op_sub(hk, t);
+      } else if constexpr (ca(k, B) != 0) {
+        h[k] = ca(k, B) > 0 ? op_sub(hk, NB) : op_add(hk, NB);
+      } else if constexpr (ca(k, C) != 0) {
+        h[k] = ca(k, C) > 0 ? op_sub(hk, NC) : op_add(hk, NC);
+      } else {
+        h[k] = hk;
+      }
     }
   });
 }
@@ -493,13 +540,11 @@ __device__ __forceinline__ Moments<T> moments(const T (&h)[Q], T rho0) {
   T sp = T(0), sm = T(0), s0 = T(0), jy = T(0), jz = T(0);
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    if constexpr (cx(k) > 0) sp = op_add(sp, h[k]);
-    else if constexpr (cx(k) < 0) sm = op_add(sm, h[k]);
-    else s0 = op_add(s0, h[k]);
-    if constexpr (cy(k) > 0) jy = op_add(jy, h[k]);
-    else if constexpr (cy(k) < 0) jy = op_sub(jy, h[k]);
-    if constexpr (cz(k) > 0) jz = op_add(jz, h[k]);
-    else if constexpr (cz(k) < 0) jz = op_sub(jz, h[k]);
+    if constexpr (cx(k) > 0) acc<1>(sp, h[k], k == first_with(0, 1));
+    else if constexpr (cx(k) < 0) acc<1>(sm, h[k], k == first_with(0, -1));
+    else acc<1>(s0, h[k], k == first_with(0, 0));
+    if constexpr (cy(k) != 0) acc<cy(k)>(jy, h[k], k == first_nonzero(1));
+    if constexpr (cz(k) != 0) acc<cz(k)>(jz, h[k], k == first_nonzero(2));
   });
   Moments<T> m;
   m.drho = op_add(op_add(sp, sm), s0);
@@ -547,13 +592,8 @@ __device__ __forceinline__ void collide(T (&h)[Q], const Moments<T>& m, T omega,
       h[k] = op_fma(keep, h[k], op_mul(op_mul(omega, wgt<T>(k)), b));
     } else if constexpr (k < o) {
       constexpr bool axis = w36(k) == 2;
-      T cj = T(0), cu = T(0);
-      if constexpr (cx(k) != 0) { cj = cx(k) > 0 ? op_add(cj, m.jx) : op_sub(cj, m.jx);
-                                  cu = cx(k) > 0 ? op_add(cu, m.ux) : op_sub(cu, m.ux); }
-      if constexpr (cy(k) != 0) { cj = cy(k) > 0 ? op_add(cj, m.jy) : op_sub(cj, m.jy);
-                                  cu = cy(k) > 0 ? op_add(cu, m.uy) : op_sub(cu, m.uy); }
-      if constexpr (cz(k) != 0) { cj = cz(k) > 0 ? op_add(cj, m.jz) : op_sub(cj, m.jz);
-                                  cu = cz(k) > 0 ? op_add(cu, m.uz) : op_sub(cu, m.uz); }
+      const T cj = dot_c<k>(m.jx, m.jy, m.jz);
+      const T cu = dot_c<k>(m.ux, m.uy, m.uz);
       const T t = op_fma(op_mul(axis ? g_axis : g_diag, cj), cu, axis ? ob_axis : ob_diag);
       T a;
       if constexpr (EXACT_MOMENTUM) {
