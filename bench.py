@@ -685,8 +685,8 @@ def study_force(args):
     import paper_0811_4593_gb300 as lbm
     _gpu_study_setup()
     rows = []
-    for tau, steps in ((2.0, 8000), (1.0, 22000)):
-        wl = inp.force_poiseuille(n=32, tau=tau, force=1e-6, wall_axis=0, flow_axis=2, other=None)
+    for tau, steps, force in ((2.0, 8000, 1e-6), (1.0, 22000, 1e-6), (2.0, 8000, 1e-5), (1.0, 22000, 1e-5)):
+        wl = inp.force_poiseuille(n=32, tau=tau, force=force, wall_axis=0, flow_axis=2, other=None)
         F = wl.force[2]
         x = np.arange(wl.nx)
         h = (wl.nx - 1) / 2.0
