@@ -834,8 +834,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS, (SweepOccupancy<S, RESID, false
 // thread. The binary16 sweep moves half the bytes of the float one for the same
 // arithmetic and is bound by instruction issue; pairing halves the index and address
 // work per node: a population with c_x = 0 is read as one aligned half2 for both
-// nodes, one with c_x != 0 as two halves from one address, and the two results of a
-// population are stored as one half2. Each node runs the single-node sweep's closure,
+// nodes, one with c_x != 0 as two halves, and the two results of a population are
+// stored as one half2. Each node runs the single-node sweep's closure,
 // moment and collision code, so both sweeps give the same bits.
 // ---------------------------------------------------------------------------------
 // Read-only loads that also ask L2 to fetch the enclosing 256-byte block (PTX
@@ -854,7 +854,11 @@ __device__ __forceinline__ void ld_half2_l2(const __half* p, float& lo, float& h
   hi = __half2float(__ushort_as_half(static_cast<unsigned short>(v >> 16)));
 }
 
-template <bool FAST>
+// Populations of both nodes of a pair. Node A = x0 pulls c_x = +1 populations from
+// xam (x0 - 1, or the wrap / clamp at the row start), node B = x0 + 1 pulls c_x = -1
+// populations from xbp (x0 + 2, or the wrap / clamp at the row end). One code path for
+// every pair: splitting off the row ends as a separate branch cost 9 % (both branches
+// ran in the warps holding a row end, and the larger body took registers).
 __device__ __forceinline__ void load_pair(const SweepArgs& a, uint32_t x0, uint32_t xam, uint32_t xbp,
                                           const uint32_t (&rows)[3][3], float (&hA)[Q], float (&hB)[Q]) {
   static_for<0, Q>([&](auto kc) {
@@ -863,13 +867,11 @@ __device__ __forceinline__ void load_pair(const SweepArgs& a, uint32_t x0, uint3
     if constexpr (cx(k) == 0) {
       ld_half2_l2(base + x0, hA[k], hB[k]);
     } else if constexpr (cx(k) > 0) {  // pulled from x - 1
-      const __half* pb = base + x0;
-      hB[k] = ld_half_l2(pb);
-      hA[k] = ld_half_l2(FAST ? pb - 1 : base + xam);
+      hB[k] = ld_half_l2(base + x0);
+      hA[k] = ld_half_l2(base + xam);
     } else {  // pulled from x + 1
-      const __half* pa = base + x0 + 1;
-      hA[k] = ld_half_l2(pa);
-      hB[k] = ld_half_l2(FAST ? pa + 1 : base + xbp);
+      hA[k] = ld_half_l2(base + x0 + 1);
+      hB[k] = ld_half_l2(base + xbp);
     }
   });
 }
@@ -901,8 +903,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) sweep_pair_kernel(const __gr
   const uint32_t xam = x0 ? x0 - 1 : (px ? a.nx - 1 : 0);
   const uint32_t xbp = (x0 + 2 < a.nx) ? x0 + 2 : (px ? 0 : a.nx - 1);
   float hA[Q], hB[Q];
-  if (x0 != 0 && x0 + 2 < a.nx) load_pair<true>(a, x0, xam, xbp, rows, hA, hB);
-  else load_pair<false>(a, x0, xam, xbp, rows, hA, hB);
+  load_pair(a, x0, xam, xbp, rows, hA, hB);
   const int fy = py ? 0 : (y == 0 ? 1 : (y == a.ny - 1 ? 2 : 0));
   const int fz = pz ? 0 : (z == 0 ? 1 : (z == a.nz - 1 ? 2 : 0));
   const int codeA = (px ? 0 : (x0 == 0 ? 1 : 0)) + 3 * fy + 9 * fz;
