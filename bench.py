@@ -711,6 +711,44 @@ def study_force(args):
           flush=True)
 
 
+def study_configs(args):
+    """Throughput of the small configurations (Couette 8x8x17, 5000 steps; plane
+    Poiseuille 4x4x256, tau 1, 15100 steps) on the GPU in each storage type and in the
+    FP64 oracle on the host cores, with the GPU-vs-oracle velocity error."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_0811_4593_gb300 as lbm
+    _gpu_study_setup()
+    rows = []
+    for name, wl, steps in (("couette 8x8x17", inp.couette(), 5000),
+                            ("poiseuille 4x4x256 tau 1", inp.poiseuille(256, 1.0), 15100)):
+        olat = oracle.Lattice.from_workload(wl)
+        t0 = time.perf_counter()
+        ref = oracle.run(olat, oracle.init_equilibrium(olat), steps)
+        dt = time.perf_counter() - t0
+        _, uo = oracle.macros(olat, ref)
+        row = {"config": name, "steps": steps, "nodes": wl.cells,
+               "oracle": {"mlups": wl.cells * steps / dt / 1e6, "threads": oracle.threads()}}
+        for prec in ("f64", "f32", "f16"):
+            with lbm.Lattice.from_workload(wl, prec) as lat:
+                lat.step(10)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(lat.stream)
+                lat.step(steps - 10)
+                e1.record(lat.stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                _, u = lat.macros()
+                u = u.double().cpu().numpy()
+            row[prec] = {"mlups": wl.cells * (steps - 10) / (ms * 1e-3) / 1e6,
+                         "max_vs_oracle": float(np.abs(u - uo).max() / np.abs(uo).max())}
+        rows.append(row)
+    print(json.dumps({"study": "small configurations", "rows": rows}), flush=True)
+
+
 def reference(args):
     """The FP64 oracle on the host cores, `--steps` timed steps after `--warmup` on the
     bounded sample of the workload; rank 0 only."""
@@ -753,7 +791,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true", help="run the serving mix instead of the sweep benchmark")
-    ap.add_argument("--study", choices=["tilted", "duct", "poiseuille", "duct-config", "force"],
+    ap.add_argument("--study", choices=["tilted", "duct", "poiseuille", "duct-config", "force", "configs"],
                     help="run a reproduction study instead of the benchmark")
     ap.add_argument("--study-steps", type=int, default=0, help="steps of the duct-config study (default 20000)")
     ap.add_argument("--requests", type=int, default=2000)
@@ -778,6 +816,8 @@ def main():
         study_duct_config(args)
     elif args.study == "force":
         study_force(args)
+    elif args.study == "configs":
+        study_configs(args)
     elif args.serving:
         serving(args)
     else:
