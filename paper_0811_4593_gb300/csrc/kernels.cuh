@@ -804,9 +804,10 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
 
 // Resident 256-thread blocks per SM each sweep variant is compiled for (the register
 // budget is 65536 / (256 * blocks)). The float sweeps are memory-bound and need many
-// warps in flight to hide DRAM latency: 6 blocks (<= 42 registers) for the plain
-// single-lattice step; the residual variant (5) and the batched variants (4) carry
-// more state and get fewer blocks so that they do not spill. The FP64 sweeps are bound by the
+// warps in flight to hide DRAM latency: 6 blocks (<= 42 registers) for the plain step,
+// single-lattice or batched (the batched kernel at 4 blocks served 14 % fewer jobs per
+// second; its spills are in the geometry path, which serving lattices do not take); the
+// residual variant carries the reduction and gets 5. The FP64 sweeps are bound by the
 // FP64 pipe and get room for their double registers.
 // The AA gather-scatter step also keeps its push targets and takes 2 blocks fewer, the
 // AA in-place step one fewer.
@@ -814,7 +815,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
 // compiled for 4 blocks (2 for FP64).
 template <typename S, bool RESID, bool BATCHED, int MODE, bool GEOM = false>
 struct SweepOccupancy {
-  static constexpr int base = BATCHED ? 4 : (RESID ? 5 : 6);
+  static constexpr int base = RESID ? 5 : 6;
   static constexpr int blocks = GEOM ? 4 : (MODE == 1 ? (base > 4 ? 4 : base - 1) : (MODE == 2 ? (base > 5 ? 5 : base) : base));
 };
 template <bool RESID, bool BATCHED, int MODE, bool GEOM>
