@@ -207,6 +207,11 @@ LBM_API lbm_status lbm_set_solid(lbm_ctx* ctx, const uint8_t* solid);
  * is attached to a batch (LBM_ERR_STATE). Synchronises. */
 LBM_API lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* solid, const int8_t* code);
 
+/* The populations the rule of a node code overwrites: bit k of *mask set for population
+ * k (the paper's f_{k+1}). Host-only, needs no device. LBM_ERR_ARG for a value that is
+ * not a code. */
+LBM_API lbm_status lbm_rule_unknowns(int code, uint32_t* mask);
+
 /* Uniform body force F (force per volume, lattice units) acting on every fluid node
  * (Sec. "Numerical Results", eq. gravity): the collision relaxes toward the equilibrium
  * at the velocity u + tau F / rho and so adds F to each node's momentum per step. The

@@ -43,6 +43,7 @@ EXPORTS = {
     "lbm_set_geometry": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_set_body_force": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "lbm_check_guards": (C.c_int, [C.c_void_p]),
+    "lbm_rule_unknowns": (C.c_int, [C.c_int, C.POINTER(C.c_uint32)]),
     "lbm_info": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_batch_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_void_p)]),

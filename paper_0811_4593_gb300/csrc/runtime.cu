@@ -679,6 +679,14 @@ lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* solid, const int8_t* co
   return LBM_OK;
 }
 
+lbm_status lbm_rule_unknowns(int code, uint32_t* mask) {
+  if (!mask) return fail(nullptr, LBM_ERR_ARG, "mask is NULL");
+  const uint32_t m = rule_unknowns(code);
+  if (!m) return fail(nullptr, LBM_ERR_ARG, "%d is not a boundary code", code);
+  *mask = m;
+  return LBM_OK;
+}
+
 lbm_status lbm_set_solid(lbm_ctx* ctx, const uint8_t* solid) {
   if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
   if (!solid) return fail(ctx, LBM_ERR_ARG, "solid is NULL");

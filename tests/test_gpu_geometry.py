@@ -191,3 +191,24 @@ def test_inconsistent_codes_are_rejected_by_the_library():
             lat.set_geometry(wl.solid, wl.code)
         with pytest.raises(lbm.LBMError):
             lat.set_body_force(wl.force)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_classified_sphere_matches_oracle(prec):
+    # a voxel sphere in a periodic box driven by a body force; its boundary codes come
+    # from the geometry classifier (whose rule sets equal the oracle's, see
+    # test_geometry_classify.py), nodes no rule covers take mid-grid bounce-back
+    from paper_0811_4593_gb300 import geometry
+    n = (32, 24, 24)
+    z, y, x = np.meshgrid(*[np.arange(k) for k in n[::-1]], indexing="ij")
+    solid = (((x - 15.5) ** 2 + (y - 11.5) ** 2 + (z - 11.5) ** 2) < 5.2 ** 2).astype(np.uint8)
+    wl = inp.make_workload("sphere", *n, 0.8, [None] * 6)
+    wl.solid = solid
+    wl.code = geometry.classify(solid, (False, False, False))
+    wl.force = np.array([2e-5, 0.0, 0.0])
+    f0 = noisy_state((19, wl.nz, wl.ny, wl.nx), 90, amp=0.005)
+    got, ref = run_pair(wl, prec, f0, 40)
+    fluid = solid == 0
+    assert velocity_error(wl, got, ref) <= TOL[prec]
+    if prec == "f64":
+        assert np.abs(got - ref)[:, fluid].max() / np.abs(ref).max() <= 1e-12
