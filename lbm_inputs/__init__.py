@@ -134,6 +134,13 @@ def couette(nx=8, ny=8, nz=17, tau=1.0, u_top=0.05, steps=5000) -> Workload:
                          meta={"u_top": u_top})
 
 
+def shear(nx=32, ny=32, nz=32, tau=1.0, u=0.02, steps=0) -> Workload:
+    """The paper's shear test: x, y periodic; the bottom plane z=0 moves with (-u, 0, 0)
+    and the top plane z=nz-1 with (+u, 0, 0)."""
+    return make_workload("shear", nx, ny, nz, tau, [None, None, None, None, (-u, 0.0, 0.0), (u, 0.0, 0.0)],
+                         steps, meta={"u": u})
+
+
 def duct(nx=256, ny=64, nz=64, tau=0.6, peak=0.05, angle_deg=30.0, steps=20000) -> Workload:
     """Square duct: velocity inlet at x=0 with a product-parabola profile of the given
     peak, tilted by ``angle_deg`` from the x axis in the x-y plane; the same profile

@@ -344,3 +344,20 @@ def test_fp32_low_viscosity_duct_within_bar():
     err = velocity_error(wl, got, ref)
     print("fp32 duct tau 0.6 velocity error", err)
     assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("prec,tau", [("f64", 1.0), ("f64", 2.0), ("f32", 1.0)])
+def test_paper_shear_32_cubed_is_linear(prec, tau):
+    # the paper's shear test at its size: 32^3, x and y periodic, planes z = 0 and 31
+    # moving with -0.02 and +0.02; a linear profile to rounding
+    import paper_0811_4593_gb300 as lbm
+    wl = inp.shear(32, 32, 32, tau, 0.02)
+    nu = (tau - 0.5) / 3.0
+    steps = int(36.0 * 31 ** 2 / (np.pi ** 2 * nu)) + 1
+    with lbm.Lattice.from_workload(wl, prec) as lat:
+        lat.step(steps)
+        _, u = lat.macros()
+        u = u.double().cpu().numpy()
+    z = np.arange(32)[:, None, None]
+    err = np.abs(u[0] - (-0.02 + 0.04 * z / 31)).max() / 0.02
+    assert err < (1e-12 if prec == "f64" else 1e-5), err

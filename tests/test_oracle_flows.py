@@ -44,6 +44,22 @@ def test_couette_is_linear_to_rounding(orc):
     assert abs(m1 - m0) / m0 < 1e-14
 
 
+@pytest.mark.parametrize("tau", [1.0, 2.0, 0.7])
+def test_opposite_wall_shear_is_linear_to_rounding(orc, tau):
+    # The paper's shear test: planes z = 0 and z = 31 moving with -0.02 and +0.02 along x,
+    # periodic x and y (4 x 4 nodes suffice for the one-dimensional flow); the profile is
+    # u_x = -0.02 + 0.04 z / 31 to rounding, for any tau.
+    wl = inp.shear(4, 4, 32, tau, 0.02)
+    lat = orc.Lattice.from_workload(wl)
+    nu = (tau - 0.5) / 3.0
+    steps = int(36.0 * 31 ** 2 / (np.pi ** 2 * nu)) + 1   # slowest mode below e^-36
+    f = orc.run(lat, orc.init_equilibrium(lat), steps)
+    _, u = orc.macros(lat, f)
+    z = np.arange(wl.nz)[:, None, None]
+    assert np.abs(u[0] - (-0.02 + 0.04 * z / 31)).max() < 1e-14
+    assert np.abs(u[1]).max() < 1e-14 and np.abs(u[2]).max() < 1e-14
+
+
 @pytest.mark.parametrize("periodic", [(False, False, False), (False, True, False), (True, False, True)])
 def test_boundary_velocity_is_exact_after_every_step(orc, periodic):
     # Face nodes carry exactly their prescribed velocity, edges and corners exactly
