@@ -390,9 +390,9 @@ def native(args):
             if p != args.precision:
                 vs[p] = run_variant(wl, p, args.variant_steps, 20, args.resid_every, d, clock)
                 torch.cuda.empty_cache()
-        vs[f"{args.precision}_aa"] = run_variant(wl, args.precision, args.variant_steps, 20, args.resid_every, d,
-                                                 clock, scheme="aa")
-        torch.cuda.empty_cache()
+        for p in dict.fromkeys((args.precision, "f16")):
+            vs[f"{p}_aa"] = run_variant(wl, p, args.variant_steps, 20, args.resid_every, d, clock, scheme="aa")
+            torch.cuda.empty_cache()
         out["variants"] = vs
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)

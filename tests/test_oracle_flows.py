@@ -60,11 +60,13 @@ def test_opposite_wall_shear_is_linear_to_rounding(orc, tau):
     assert np.abs(u[1]).max() < 1e-14 and np.abs(u[2]).max() < 1e-14
 
 
+@pytest.mark.parametrize("tau", [0.55, 0.8, 1.5])
 @pytest.mark.parametrize("periodic", [(False, False, False), (False, True, False), (True, False, True)])
-def test_boundary_velocity_is_exact_after_every_step(orc, periodic):
+def test_boundary_velocity_is_exact_after_every_step(orc, periodic, tau):
     # Face nodes carry exactly their prescribed velocity, edges and corners exactly
-    # zero, after streaming, closure and collision.
-    wl = inp.random_face_workload(3, 7, 6, 5, 0.8, periodic)
+    # zero, after streaming, closure and collision, whatever tau (the closure does not
+    # depend on it, and the wall is on the node).
+    wl = inp.random_face_workload(3, 7, 6, 5, tau, periodic)
     lat = orc.Lattice.from_workload(wl)
     faces, edge, corner = boundary_masks(wl)
     f = noisy_state(orc, lat, 5)
