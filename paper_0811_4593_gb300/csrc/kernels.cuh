@@ -874,11 +874,14 @@ __device__ __forceinline__ void ld_half2_l2(const __half* p, float& lo, float& h
 // populations from xbp (x0 + 2, or the wrap / clamp at the row end). One code path for
 // every pair: splitting off the row ends as a separate branch cost 9 % (both branches
 // ran in the warps holding a row end, and the larger body took registers).
+// MODE STREAM_AA_GATHER reads slot -k of the source node instead of slot k.
+template <int MODE>
 __device__ __forceinline__ void load_pair(const SweepArgs& a, uint32_t x0, uint32_t xam, uint32_t xbp,
                                           const uint32_t (&rows)[3][3], float (&hA)[Q], float (&hB)[Q]) {
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    const __half* base = static_cast<const __half*>(a.src_pop[k]) + rows[1 - cz(k)][1 - cy(k)];
+    constexpr int slot = MODE == STREAM_AA_GATHER ? opp(k) : k;
+    const __half* base = static_cast<const __half*>(a.src_pop[slot]) + rows[1 - cz(k)][1 - cy(k)];
     if constexpr (cx(k) == 0) {
       ld_half2_l2(base + x0, hA[k], hB[k]);
     } else if constexpr (cx(k) > 0) {  // pulled from x - 1
@@ -891,7 +894,10 @@ __device__ __forceinline__ void load_pair(const SweepArgs& a, uint32_t x0, uint3
   });
 }
 
-template <typename S>
+// MODE: STREAM_AB (pull from the other array), STREAM_AA_GATHER (read slot -k of node
+// x - c_k, write f*_k to slot k of node x + c_k) or STREAM_AA_LOCAL (read and write the
+// pair's own slots, k and -k exchanged), as in the single-node sweep.
+template <typename S, int MODE>
 __global__ void __launch_bounds__(SWEEP_THREADS, 4) sweep_pair_kernel(const __grid_constant__ SweepArgs a) {
   static_assert(std::is_same<S, __half>::value, "the paired sweep is for binary16 storage");
   const uint32_t pair = blockIdx.x * SWEEP_THREADS + threadIdx.x;
@@ -906,7 +912,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) sweep_pair_kernel(const __gr
   const uint32_t yp = (y + 1 < a.ny) ? y + 1 : (py ? 0 : a.ny - 1);
   const uint32_t zm = z ? z - 1 : (pz ? a.nz - 1 : 0);
   const uint32_t zp = (z + 1 < a.nz) ? z + 1 : (pz ? 0 : a.nz - 1);
-  // rows[1 - c_z][1 - c_y]: start of the row a population is pulled from
+  // rows[1 - c_z][1 - c_y]: start of the row a population is pulled from;
+  // rows[1 + c_z][1 + c_y]: the row the AA gather step pushes it to
   const uint32_t zs[3] = {zm, z, zp}, ys[3] = {ym, y, yp};
   uint32_t rows[3][3];
 #pragma unroll
@@ -918,11 +925,20 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) sweep_pair_kernel(const __gr
   const uint32_t xam = x0 ? x0 - 1 : (px ? a.nx - 1 : 0);
   const uint32_t xbp = (x0 + 2 < a.nx) ? x0 + 2 : (px ? 0 : a.nx - 1);
   float hA[Q], hB[Q];
-  load_pair(a, x0, xam, xbp, rows, hA, hB);
+  if constexpr (MODE == STREAM_AA_LOCAL) {
+    static_for<0, Q>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      ld_half2_l2(static_cast<const __half*>(a.src_pop[k]) + cell, hA[k], hB[k]);
+    });
+  } else {
+    load_pair<MODE>(a, x0, xam, xbp, rows, hA, hB);
+  }
+  const int fxA = px ? 0 : (x0 == 0 ? 1 : 0);
+  const int fxB = px ? 0 : (x0 + 1 == a.nx - 1 ? 2 : 0);
   const int fy = py ? 0 : (y == 0 ? 1 : (y == a.ny - 1 ? 2 : 0));
   const int fz = pz ? 0 : (z == 0 ? 1 : (z == a.nz - 1 ? 2 : 0));
-  const int codeA = (px ? 0 : (x0 == 0 ? 1 : 0)) + 3 * fy + 9 * fz;
-  const int codeB = (px ? 0 : (x0 + 1 == a.nx - 1 ? 2 : 0)) + 3 * fy + 9 * fz;
+  const int codeA = fxA + 3 * fy + 9 * fz;
+  const int codeB = fxB + 3 * fy + 9 * fz;
   if (codeA != 0) apply_boundary(codeA, a, x0, y, z, hA);
   if (codeB != 0) apply_boundary(codeB, a, x0 + 1, y, z, hB);
   const Moments<float> mA = moments(hA, a.rho0f);
@@ -931,7 +947,28 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) sweep_pair_kernel(const __gr
   collide(hB, mB, a.omegaf);
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    *reinterpret_cast<__half2*>(static_cast<__half*>(a.dst_pop[k]) + cell) = __floats2half2_rn(hA[k], hB[k]);
+    if constexpr (MODE == STREAM_AB) {
+      *reinterpret_cast<__half2*>(static_cast<__half*>(a.dst_pop[k]) + cell) = __floats2half2_rn(hA[k], hB[k]);
+    } else if constexpr (MODE == STREAM_AA_LOCAL) {
+      *reinterpret_cast<__half2*>(static_cast<__half*>(a.dst_pop[opp(k)]) + cell) =
+          __floats2half2_rn(hA[k], hB[k]);
+    } else {
+      // push f*_k to slot k of node x + c_k; a target beyond a walled face does not exist
+      const bool in_yz = !((fy == 1 && cy(k) < 0) || (fy == 2 && cy(k) > 0) || (fz == 1 && cz(k) < 0) ||
+                           (fz == 2 && cz(k) > 0));
+      if (in_yz) {
+        __half* row = static_cast<__half*>(a.dst_pop[k]) + rows[1 + cz(k)][1 + cy(k)];
+        if constexpr (cx(k) == 0) {
+          *reinterpret_cast<__half2*>(row + x0) = __floats2half2_rn(hA[k], hB[k]);
+        } else if constexpr (cx(k) > 0) {  // A -> x0 + 1, B -> x0 + 2
+          row[x0 + 1] = __float2half_rn(hA[k]);
+          if (fxB != 2) row[xbp] = __float2half_rn(hB[k]);
+        } else {  // A -> x0 - 1, B -> x0
+          if (fxA != 1) row[xam] = __float2half_rn(hA[k]);
+          row[x0] = __float2half_rn(hB[k]);
+        }
+      }
+    }
   });
 }
 
@@ -1063,8 +1100,11 @@ void launch_sweep_mode(const SweepArgs& a, bool resid, cudaStream_t s) {
 template <typename S>
 cudaError_t launch_sweep_impl(const SweepArgs& a, bool resid, int mode, cudaStream_t s) {
   if constexpr (std::is_same<S, __half>::value) {
-    if (mode == STREAM_AB && !resid && !a.links && !a.forced && (a.nx & 1u) == 0) {
-      sweep_pair_kernel<S><<<sweep_blocks(a.N >> 1), SWEEP_THREADS, 0, s>>>(a);
+    if (!resid && !a.links && !a.forced && (a.nx & 1u) == 0) {
+      const uint32_t blocks = sweep_blocks(a.N >> 1);
+      if (mode == STREAM_AA_GATHER) sweep_pair_kernel<S, STREAM_AA_GATHER><<<blocks, SWEEP_THREADS, 0, s>>>(a);
+      else if (mode == STREAM_AA_LOCAL) sweep_pair_kernel<S, STREAM_AA_LOCAL><<<blocks, SWEEP_THREADS, 0, s>>>(a);
+      else sweep_pair_kernel<S, STREAM_AB><<<blocks, SWEEP_THREADS, 0, s>>>(a);
       return cudaGetLastError();
     }
   }

@@ -62,3 +62,20 @@ def test_paired_sweep_matches_oracle(name):
     got, ref = run_pair(wl, "f16", f0, 30)
     assert velocity_error(wl, got, ref) <= 5e-3
     assert np.isfinite(decode(encode(got, "f16"), "f16")).all()
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_paired_aa_steps_equal_ab_steps(name):
+    # the paired sweep also runs both AA steps of an even-nx binary16 lattice; the AA
+    # lattice must hold the A/B lattice's bits after every pair of steps
+    import paper_0811_4593_gb300 as lbm
+    wl = WORKLOADS[name]()
+    s0 = encode(noisy_state((19, wl.nz, wl.ny, wl.nx), 4, u=(0.01, -0.004, 0.006)), "f16")
+    with lbm.Lattice.from_workload(wl, "f16") as ab, lbm.Lattice.from_workload(wl, "f16", scheme="aa") as aa:
+        ab.set_populations(s0)
+        aa.set_populations(s0)
+        for n in (2, 6):
+            ab.step(n)
+            aa.step(n)
+            np.testing.assert_array_equal(aa.get_populations(), ab.get_populations())
+        assert aa.step_residual(2) == ab.step_residual(2)
