@@ -258,9 +258,9 @@ def profiled_fp64_per_node(wl_name: str):
 
 def sweep_kernel_name(wl, precision, scheme="ab"):
     """The kernel that runs the plain (non-residual) steps of a lattice."""
-    if precision == "f16" and scheme == "ab" and wl.nx % 2 == 0 and getattr(wl, "solid", None) is None \
+    if precision == "f16" and wl.nx % 2 == 0 and getattr(wl, "solid", None) is None \
             and getattr(wl, "force", None) is None:
-        return "sweep_pair_kernel<f16>"
+        return "sweep_pair_kernel<f16>" + ("" if scheme == "ab" else " (AA steps)")
     return f"sweep_kernel<{precision}>"
 
 
