@@ -88,7 +88,12 @@ def percentile(values, q):
 class Server:
     def __init__(self, precision: str = "f32", capacity: int = 256, budget_bytes: float = 150e9,
                  round_steps: int = 100, max_steps: int = 20000, target: float = 1e-8, plateau_checks: int = 10,
-                 plateau_ceiling: float = 1e-5, keep_populations: bool = False, scheme: str = "ab"):
+                 plateau_ceiling: float = 1e-5, keep_populations: bool = False, scheme: str = "ab",
+                 batch_factory=None, lattice_factory=None):
+        """``batch_factory(capacity, precision)`` and ``lattice_factory(workload, precision,
+        scheme)`` default to the library's Batch and Lattice.from_workload; other objects
+        with the same methods can stand in for them (the scheduling logic is tested on the
+        host that way)."""
         self.precision = precision
         self.capacity = int(capacity)
         self.budget = float(budget_bytes)
@@ -99,6 +104,9 @@ class Server:
         self.plateau_ceiling = float(plateau_ceiling)
         self.keep_populations = keep_populations
         self.scheme = scheme
+        self.batch_factory = batch_factory or (lambda capacity, precision: Batch(capacity, precision))
+        self.lattice_factory = lattice_factory or (
+            lambda workload, precision, scheme: Lattice.from_workload(workload, precision, scheme=scheme))
 
     def serve(self, jobs, closed_loop: bool = False, clock=time.perf_counter, idle_sleep=0.001):
         """Run every job to completion. ``closed_loop`` ignores arrival times (all jobs
@@ -112,7 +120,7 @@ class Server:
         node_updates = 0
         peak_active = 0
         peak_bytes = 0
-        batch = Batch(self.capacity, self.precision)
+        batch = self.batch_factory(self.capacity, self.precision)
         t0 = clock()
         try:
             while pending or waiting or active:
@@ -129,7 +137,7 @@ class Server:
                     if used + need > self.budget:
                         break
                     job = waiting.popleft()
-                    lat = Lattice.from_workload(job.workload, self.precision, scheme=self.scheme)
+                    lat = self.lattice_factory(job.workload, self.precision, self.scheme)
                     slot = free.pop(0)
                     batch.attach(slot, lat)
                     active[slot] = _Active(job, lat, clock() - t0, need)
