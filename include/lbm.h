@@ -226,6 +226,13 @@ LBM_API lbm_status lbm_set_body_force(lbm_ctx* ctx, const double force[3]);
  * changed -- evidence of a write outside a buffer. Synchronises. */
 LBM_API lbm_status lbm_check_guards(lbm_ctx* ctx);
 
+/* Out-of-range indices the sweeps met since the last call, on the current device. The
+ * library built with LBM_DEBUG_BOUNDS (build option debug_bounds) checks every
+ * population, table and geometry-word index of its sweeps, replaces an index beyond
+ * its buffer by 0 and counts it; *enabled says whether this library is such a build
+ * (otherwise *count is 0). Synchronises the device. */
+LBM_API lbm_status lbm_debug_bounds_errors(int* enabled, uint64_t* count);
+
 /* Block the host until the context's stream is idle; reports asynchronous errors. */
 LBM_API lbm_status lbm_sync(lbm_ctx* ctx);
 

@@ -14,7 +14,8 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "liblbm.so")
+# LBM_LIBRARY selects another build of the library (the index-checking debug build)
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(HERE, "liblbm.so")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_STATE = 0, -1, -2, -3, -4, -5
 PRECISIONS = {"f64": 0, "f32": 1, "f16": 2}
@@ -44,6 +45,7 @@ EXPORTS = {
     "lbm_set_body_force": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "lbm_check_guards": (C.c_int, [C.c_void_p]),
     "lbm_rule_unknowns": (C.c_int, [C.c_int, C.POINTER(C.c_uint32)]),
+    "lbm_debug_bounds_errors": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_uint64)]),
     "lbm_info": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_batch_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
@@ -100,6 +102,14 @@ _hooks = None
 
 def library_path() -> str:
     return LIB_PATH
+
+
+def debug_bounds_errors():
+    """(enabled, count): whether the loaded library is the index-checking debug build,
+    and the out-of-range indices its sweeps met since the last call."""
+    en, n = C.c_int(), C.c_uint64()
+    check(lib().lbm_debug_bounds_errors(C.byref(en), C.byref(n)))
+    return bool(en.value), int(n.value)
 
 
 def lib():

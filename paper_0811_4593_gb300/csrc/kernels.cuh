@@ -42,6 +42,21 @@ __device__ __forceinline__ double op_mul(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float op_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double op_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// Index checks of the debug build (LBM_DEBUG_BOUNDS): an index at or beyond its limit
+// is counted in this translation unit's error word and replaced by 0, so the access
+// stays inside the buffer; lbm_debug_bounds_errors reads the count. The release build
+// compiles the check away.
+#ifdef LBM_DEBUG_BOUNDS
+static __device__ unsigned int g_bounds_errors;
+__device__ __forceinline__ uint32_t chk(uint32_t i, uint32_t limit) {
+  if (i < limit) return i;
+  atomicAdd(&g_bounds_errors, 1u);
+  return 0u;
+}
+#else
+__device__ __forceinline__ uint32_t chk(uint32_t i, uint32_t) { return i; }
+#endif
+
 // Signed sums whose first term is taken as it is (negation is exact), so that no
 // rounded addition of zero is ever issued.
 template <int SGN, typename T>
@@ -317,7 +332,8 @@ __device__ __forceinline__ FaceVals<T> face_values(const SweepArgs& a, uint32_t 
     const uint32_t t1 = (A == 0) ? y : x;
     const uint32_t t2 = (A == 2) ? y : z;
     const uint32_t n1 = (A == 0) ? a.ny : a.nx;
-    const FaceNode* p = fb.tab + (size_t(t2) * n1 + t1);
+    const uint32_t n2 = (A == 2) ? a.ny : a.nz;
+    const FaceNode* p = fb.tab + chk(t2 * n1 + t1, n1 * n2);
     if constexpr (std::is_same<T, double>::value) {
       const double2 a0 = __ldg(reinterpret_cast<const double2*>(p));
       const double2 a1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
@@ -724,11 +740,11 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
       const uint32_t sx = cx(k) > 0 ? xm : (cx(k) < 0 ? xp : x);
       const uint32_t sy = cy(k) > 0 ? ym : (cy(k) < 0 ? yp : y);
       const uint32_t sz = cz(k) > 0 ? zm : (cz(k) < 0 ? zp : z);
-      return (sz * a.ny + sy) * a.nx + sx;
+      return chk((sz * a.ny + sy) * a.nx + sx, a.N);
     };
     // geometry word (A/B lattices with a geometry only; 0 everywhere else)
     uint32_t lm = 0u;
-    if constexpr (GEOM) lm = a.links ? __ldg(a.links + cell) : 0u;
+    if constexpr (GEOM) lm = a.links ? __ldg(a.links + chk(cell, a.N)) : 0u;
     T h[Q];
     if (!GEOM || (lm & ~(RULE_BITS << RULE_SHIFT)) == 0u) {
       static_for<0, Q>([&](auto kc) {
@@ -881,15 +897,16 @@ __device__ __forceinline__ void load_pair(const SweepArgs& a, uint32_t x0, uint3
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     constexpr int slot = MODE == STREAM_AA_GATHER ? opp(k) : k;
-    const __half* base = static_cast<const __half*>(a.src_pop[slot]) + rows[1 - cz(k)][1 - cy(k)];
+    const __half* base = static_cast<const __half*>(a.src_pop[slot]);
+    const uint32_t row = rows[1 - cz(k)][1 - cy(k)];
     if constexpr (cx(k) == 0) {
-      ld_half2_l2(base + x0, hA[k], hB[k]);
+      ld_half2_l2(base + chk(row + x0, a.N - 1), hA[k], hB[k]);
     } else if constexpr (cx(k) > 0) {  // pulled from x - 1
-      hB[k] = ld_half_l2(base + x0);
-      hA[k] = ld_half_l2(base + xam);
+      hB[k] = ld_half_l2(base + chk(row + x0, a.N));
+      hA[k] = ld_half_l2(base + chk(row + xam, a.N));
     } else {  // pulled from x + 1
-      hA[k] = ld_half_l2(base + x0 + 1);
-      hB[k] = ld_half_l2(base + xbp);
+      hA[k] = ld_half_l2(base + chk(row + x0 + 1, a.N));
+      hB[k] = ld_half_l2(base + chk(row + xbp, a.N));
     }
   });
 }
@@ -928,7 +945,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) sweep_pair_kernel(const __gr
   if constexpr (MODE == STREAM_AA_LOCAL) {
     static_for<0, Q>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
-      ld_half2_l2(static_cast<const __half*>(a.src_pop[k]) + cell, hA[k], hB[k]);
+      ld_half2_l2(static_cast<const __half*>(a.src_pop[k]) + chk(cell, a.N - 1), hA[k], hB[k]);
     });
   } else {
     load_pair<MODE>(a, x0, xam, xbp, rows, hA, hB);
@@ -948,24 +965,26 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) sweep_pair_kernel(const __gr
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     if constexpr (MODE == STREAM_AB) {
-      *reinterpret_cast<__half2*>(static_cast<__half*>(a.dst_pop[k]) + cell) = __floats2half2_rn(hA[k], hB[k]);
+      *reinterpret_cast<__half2*>(static_cast<__half*>(a.dst_pop[k]) + chk(cell, a.N - 1)) =
+          __floats2half2_rn(hA[k], hB[k]);
     } else if constexpr (MODE == STREAM_AA_LOCAL) {
-      *reinterpret_cast<__half2*>(static_cast<__half*>(a.dst_pop[opp(k)]) + cell) =
+      *reinterpret_cast<__half2*>(static_cast<__half*>(a.dst_pop[opp(k)]) + chk(cell, a.N - 1)) =
           __floats2half2_rn(hA[k], hB[k]);
     } else {
       // push f*_k to slot k of node x + c_k; a target beyond a walled face does not exist
       const bool in_yz = !((fy == 1 && cy(k) < 0) || (fy == 2 && cy(k) > 0) || (fz == 1 && cz(k) < 0) ||
                            (fz == 2 && cz(k) > 0));
       if (in_yz) {
-        __half* row = static_cast<__half*>(a.dst_pop[k]) + rows[1 + cz(k)][1 + cy(k)];
+        __half* pop = static_cast<__half*>(a.dst_pop[k]);
+        const uint32_t row = rows[1 + cz(k)][1 + cy(k)];
         if constexpr (cx(k) == 0) {
-          *reinterpret_cast<__half2*>(row + x0) = __floats2half2_rn(hA[k], hB[k]);
+          *reinterpret_cast<__half2*>(pop + chk(row + x0, a.N - 1)) = __floats2half2_rn(hA[k], hB[k]);
         } else if constexpr (cx(k) > 0) {  // A -> x0 + 1, B -> x0 + 2
-          row[x0 + 1] = __float2half_rn(hA[k]);
-          if (fxB != 2) row[xbp] = __float2half_rn(hB[k]);
+          pop[chk(row + x0 + 1, a.N)] = __float2half_rn(hA[k]);
+          if (fxB != 2) pop[chk(row + xbp, a.N)] = __float2half_rn(hB[k]);
         } else {  // A -> x0 - 1, B -> x0
-          if (fxA != 1) row[xam] = __float2half_rn(hA[k]);
-          row[x0] = __float2half_rn(hB[k]);
+          if (fxA != 1) pop[chk(row + xam, a.N)] = __float2half_rn(hA[k]);
+          pop[chk(row + x0, a.N)] = __float2half_rn(hB[k]);
         }
       }
     }
@@ -1184,6 +1203,19 @@ int batched_grid_impl() {
   return sms * best;
 }
 
+// Count of out-of-range indices this translation unit's kernels met (debug build; the
+// count is reset by the read), or 0 in the release build.
+static inline uint32_t bounds_errors_impl() {
+#ifdef LBM_DEBUG_BOUNDS
+  unsigned int v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_bounds_errors, sizeof v) != cudaSuccess) return ~0u;
+  if (cudaMemcpyToSymbol(g_bounds_errors, &zero, sizeof zero) != cudaSuccess) return ~0u;
+  return v;
+#else
+  return 0u;
+#endif
+}
+
 #define LBM_INSTANTIATE(S)                                                                              \
   template <> cudaError_t launch_sweep<S>(const SweepArgs& a, bool resid, int mode, cudaStream_t s) {   \
     return launch_sweep_impl<S>(a, resid, mode, s);                                                     \
@@ -1204,6 +1236,7 @@ int batched_grid_impl() {
                                                   cudaStream_t s) {                                     \
     return launch_sweep_batched_impl<S>(hdr, ents, parity, resid, mode, grid, s);                      \
   }                                                                                                     \
-  template <> int batched_grid<S>() { return batched_grid_impl<S>(); }
+  template <> int batched_grid<S>() { return batched_grid_impl<S>(); }                                  \
+  template <> uint32_t bounds_errors<S>() { return bounds_errors_impl(); }
 
 }  // namespace lbm

@@ -115,6 +115,7 @@ cudaError_t launch_final_reduce(const double* partials, uint32_t nblocks, double
 template <typename S> cudaError_t launch_sweep_batched(const BatchHeader* hdr, const BatchEntry* ents, uint32_t parity,
                                                        bool resid, int mode, int grid, cudaStream_t s);
 template <typename S> int batched_grid();  // persistent grid size: SMs x resident blocks per SM
+template <typename S> uint32_t bounds_errors();  // debug build: indices out of range (read resets)
 cudaError_t launch_batch_final_reduce(const BatchHeader* hdr, const BatchEntry* ents, int capacity, double* results,
                                       cudaStream_t s);
 

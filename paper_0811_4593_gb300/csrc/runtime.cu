@@ -736,6 +736,27 @@ lbm_status lbm_check_guards(lbm_ctx* ctx) {
   return LBM_OK;
 }
 
+lbm_status lbm_debug_bounds_errors(int* enabled, uint64_t* count) {
+  if (!enabled || !count) return fail(nullptr, LBM_ERR_ARG, "enabled or count is NULL");
+#ifdef LBM_DEBUG_BOUNDS
+  *enabled = 1;
+#else
+  *enabled = 0;
+#endif
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, LBM_ERR_CUDA, "device synchronisation failed");
+  }
+  const uint32_t c[3] = {lbm::bounds_errors<double>(), lbm::bounds_errors<float>(), lbm::bounds_errors<__half>()};
+  uint64_t total = 0;
+  for (uint32_t v : c) {
+    if (v == ~0u) return fail(nullptr, LBM_ERR_CUDA, "reading the bounds-error words failed");
+    total += v;
+  }
+  *count = total;
+  return LBM_OK;
+}
+
 lbm_status lbm_sync(lbm_ctx* ctx) {
   if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
   DeviceGuard g(ctx->device);
