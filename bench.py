@@ -474,7 +474,8 @@ def study_tilted(args):
     """The paper's tilted-channel comparison: xi of the on-site closure (GPU, FP64) at
     the paper's size and at twice its resolution, of the straight channel, of the inflow
     restricted to the plane normal, and of the N = 0 closure (FP64 oracle on the host:
-    a comparison closure the CUDA path does not carry)."""
+    a comparison closure the CUDA path does not carry). The normal-only inflow is taken
+    both as the z component of the profile and as its full speed along z."""
     import torch
 
     import paper_0811_4593_gb300 as lbm
@@ -483,7 +484,8 @@ def study_tilted(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     cases = [("on_site", inp.tilted_channel(), 20000), ("on_site_2x", inp.tilted_channel(scale=2), 80000),
              ("straight", inp.tilted_channel(shift=0), 20000),
-             ("normal_only", inp.tilted_channel(normal_only=True), 20000)]
+             ("normal_only", inp.tilted_channel(normal_only=True), 20000),
+             ("normal_only_magnitude", inp.tilted_channel(normal_only="magnitude"), 20000)]
     out = {"study": "tilted channel (Sec. Numerical Results)", "tau": 1.0, "u0": 0.01,
            "xi": {}, "xi_near_planes": {}, "seconds": {}}
     for name, wl, steps in cases:

@@ -188,8 +188,9 @@ def tilted_channel(scale: int = 1, tau: float = 1.0, u0: float = 0.01, shift: in
     Fluid nodes satisfy |x - x_c(z)| < w/2 with x_c(z) = x0 + g (z - z0), (x0, z0) the
     centre of the domain, g = shift / 127, w = 20 (all lengths times ``scale``). The
     profile is v(x) = u0 [1 - ((x - x_c(z)) / (w/2))^2] along (g, 0, 1) / |(g, 0, 1)|
-    (eq. pois); ``normal_only`` keeps only its z component (the comparison inflow
-    restricted to the plane normal)."""
+    (eq. pois). ``normal_only`` gives the comparison inflow restricted to the plane
+    normal: True (or "component") keeps the profile's z component, "magnitude" puts its
+    full speed along z."""
     nx, ny, nz = 64 * scale, 8 * scale, 128 * scale
     g = shift / 127.0
     half = 10.0 * scale
@@ -201,6 +202,10 @@ def tilted_channel(scale: int = 1, tau: float = 1.0, u0: float = 0.01, shift: in
     direction = np.array([g, 0.0, 1.0]) / math.hypot(g, 1.0)
     prof = np.where(solid == 0, u0 * (1.0 - d * d), 0.0)          # [z][y][x]
     vel = prof[..., None] * direction                               # [z][y][x][3]
+    if normal_only not in (False, True, "component", "magnitude"):
+        raise ValueError("normal_only must be False, True, 'component' or 'magnitude'")
+    if normal_only == "magnitude":
+        vel[..., 2] = prof
     if normal_only:
         vel[..., 0] = 0.0
         vel[..., 1] = 0.0

@@ -52,3 +52,17 @@ def test_inflow_plane_carries_the_prescribed_profile(orc):
     _, u = orc.macros(lat, f)
     fluid0 = wl.solid[0] == 0
     np.testing.assert_allclose(u[:, 0][:, fluid0].T, wl.utabs[4][fluid0], rtol=0, atol=1e-16)
+
+
+def test_normal_only_inflow_readings():
+    # the comparison inflow restricted to the plane normal: the profile's z component,
+    # or its full speed along z; both with no tangential part, same nodes as the tilted one
+    full = inp.tilted_channel(steps=0)
+    comp = inp.tilted_channel(steps=0, normal_only=True)
+    mag = inp.tilted_channel(steps=0, normal_only="magnitude")
+    for fc in (4, 5):
+        t, c, m = full.utabs[fc], comp.utabs[fc], mag.utabs[fc]
+        assert not c[..., :2].any() and not m[..., :2].any()
+        np.testing.assert_array_equal(c[..., 2], t[..., 2])
+        np.testing.assert_allclose(m[..., 2], np.sqrt((t ** 2).sum(-1)), rtol=1e-15, atol=0)
+        assert (m[..., 2] >= c[..., 2]).all() and (m[..., 2] > c[..., 2]).any()
