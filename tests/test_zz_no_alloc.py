@@ -14,7 +14,6 @@ the first call wrote is what the second one compares against.
 import ctypes as C
 import math
 
-import numpy as np
 import pytest
 
 import lbm_inputs as inp
