@@ -118,8 +118,8 @@ def lib():
     with _lock:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
-                raise RuntimeError(f"{LIB_PATH} is not built: run `python -c \"import __graft_entry__ as g; "
-                                   f"g.build()\"` (needs nvcc)")
+                raise RuntimeError(f"{LIB_PATH} is not built: run `python -m paper_0811_4593_gb300.build` "
+                                   f"(needs nvcc)")
             L = C.CDLL(LIB_PATH)
             for name, (res, args) in EXPORTS.items():
                 fn = getattr(L, name)
