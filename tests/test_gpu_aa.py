@@ -1,15 +1,19 @@
 """GPU tests of AA-pattern streaming (one population array, steps in pairs).
 
-The AA scheme performs exactly the arithmetic of the A/B scheme on the same values and
-only moves them differently through memory, so after every pair of steps its state,
-macroscopic fields and residuals must equal the A/B ones bit for bit; the populations
-it holds take half the device memory.
+AA lattices are checked against the FP64 oracle element by element (populations,
+macroscopic fields and the residual reduction after an even number of steps, from the
+same stored state, with the tolerances of the A/B parity tests), for the single-node
+AA steps and for the paired binary16 AA steps (even nx). The AA scheme also performs
+exactly the arithmetic of the A/B scheme on the same values and only moves them
+differently through memory, so after every pair of steps its state, macroscopic
+fields and residuals must equal the A/B ones bit for bit; the populations it holds
+take half the device memory.
 """
 import numpy as np
 import pytest
 
 import lbm_inputs as inp
-from lbm_testlib import encode, noisy_state
+from lbm_testlib import decode, encode, noisy_state, population_error, velocity_error
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +35,17 @@ WORKLOADS = {
     "periodic": lambda: inp.make_workload("periodic", 9, 7, 5, 0.6, [None] * 6),
     "couette": lambda: inp.couette(),
     "minimum": lambda: inp.random_face_workload(29, 3, 3, 3, 1.0, (False, False, False)),
+    # even nx: binary16 lattices take the paired AA steps
+    "duct_even": lambda: inp.duct(36, 19, 23, 0.8, 0.05, 30.0),
 }
+# steps of the oracle comparison (even: an AA lattice is observable between pairs)
+ORACLE_STEPS = {"duct": 40, "channel": 40, "pressure": 26, "periodic": 30, "couette": 60, "minimum": 20,
+                "duct_even": 40}
+# velocity error bars against the oracle, as in the A/B parity tests: FP64 and FP32 at
+# the fixed bars, binary16 storage at about twice the error measured for each case
+TOL = {"f64": 1e-12, "f32": 1e-5}
+F16_TOL = {"duct": 6e-4, "channel": 8e-4, "pressure": 6e-4, "periodic": 9e-4, "couette": 3e-4, "minimum": 2e-4,
+           "duct_even": 6e-4}
 
 
 def make(wl, prec, scheme, seed):
@@ -39,6 +53,54 @@ def make(wl, prec, scheme, seed):
     lat = lbm.Lattice.from_workload(wl, prec, scheme=scheme)
     lat.set_populations(encode(noisy_state((19, wl.nz, wl.ny, wl.nx), seed, u=(0.01, -0.004, 0.006)), prec))
     return lat
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_aa_matches_oracle(name, prec):
+    import oracle
+    import paper_0811_4593_gb300 as lbm
+    wl = WORKLOADS[name]()
+    steps = ORACLE_STEPS[name]
+    tol = F16_TOL[name] if prec == "f16" else TOL[prec]
+    s0 = encode(noisy_state((19, wl.nz, wl.ny, wl.nx), 300 + list(WORKLOADS).index(name),
+                            u=(0.01, -0.004, 0.006)), prec, wl.rho0)
+    olat = oracle.Lattice.from_workload(wl)
+    half = 2 * (steps // 4)                  # an even split of the steps
+    mid = oracle.run(olat, decode(s0, prec, wl.rho0), half)
+    with lbm.Lattice.from_workload(wl, prec, scheme="aa") as lat:
+        assert lat.info()["scheme"] == 1
+        lat.set_populations(s0)
+        lat.step(half)
+        got_mid = decode(lat.get_populations(), prec, wl.rho0)
+        r_mid, _ = lat.residual()            # snapshot <- velocities of the mid state
+        lat.step(steps - half)
+        got = decode(lat.get_populations(), prec, wl.rho0)
+        rho, u = lat.macros()
+        rho, u = rho.double().cpu().numpy(), u.double().cpu().numpy()
+        r_end, m_end = lat.residual()
+    ref = oracle.run(olat, mid, steps - half)
+    for g, r in ((got_mid, mid), (got, ref)):
+        ev = velocity_error(wl, g, r)
+        assert ev <= tol, f"{name} {prec} AA: velocity error {ev:.3e}"
+        if prec == "f64":
+            assert population_error(g, r) <= 1e-12
+    # macroscopic fields of the AA state (read from its swapped slots) against the
+    # oracle's moments of the oracle state
+    rref, uref = oracle.macros(olat, ref)
+    scale = np.abs(uref).max()
+    assert np.abs(u - uref).max() <= tol * scale
+    assert np.abs(rho - rref).max() <= (1e-12 if prec == "f64" else tol)
+    # the residual reduction of the AA state against the oracle's, both on the GPU's
+    # own states (so that trajectory differences do not enter). The residual is a
+    # velocity difference in units of the velocity magnitude, so its bar is absolute:
+    # the float snapshot of the mid state carries rounding of order 1e-7 |u|.
+    assert r_mid == pytest.approx(1.0, abs=1e-12)
+    _, u_mid = oracle.macros(olat, got_mid)
+    red = oracle.reduce(olat, got, u_mid)
+    bar = 1e-12 if prec == "f64" else 1e-5
+    assert m_end == pytest.approx(red[0], rel=bar)
+    assert abs(r_end - np.sqrt(red[1]) / np.sqrt(red[2])) <= bar
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16"])

@@ -13,7 +13,7 @@ from lbm_testlib import decode, encode, noisy_state, velocity_error
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 5e-3}
+TOL = {"f64": 1e-12, "f32": 1e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -7,7 +7,14 @@ from lbm_testlib import decode, encode, noisy_state, run_pair, velocity_error
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 5e-3}
+TOL = {"f64": 1e-12, "f32": 1e-5}
+# binary16 storage: about twice the velocity error measured for each case (GB300:
+# tilted 2.6e-4, obstacles 3.1e-4, pillars 1.1e-4 / 2.8e-4 / 2.9e-4, sphere 3.8e-4)
+F16_TOL = {"tilted": 5e-4, "obstacles": 6e-4, "pillar0": 3e-4, "pillar1": 6e-4, "pillar2": 6e-4, "sphere": 8e-4}
+
+
+def tol(case, prec):
+    return F16_TOL[case] if prec == "f16" else TOL[prec]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -36,7 +43,7 @@ def test_solid_nodes_match_oracle(name, prec):
     f0 = noisy_state((19, wl.nz, wl.ny, wl.nx), 70, amp=0.01, u=(0.002, 0.0, 0.004))
     got, ref = run_pair(wl, prec, f0, 30, form=1)
     fluid = wl.solid == 0
-    assert velocity_error(wl, got, ref) <= TOL[prec]
+    assert velocity_error(wl, got, ref) <= tol(name, prec)
     if prec == "f64":
         assert np.abs(got - ref)[:, fluid].max() / np.abs(ref).max() <= 1e-12
     # solid nodes are carried unchanged, bit for bit
@@ -71,7 +78,7 @@ def test_pillar_rules_match_oracle(axis, prec):
     f0 = noisy_state((19, wl.nz, wl.ny, wl.nx), 80 + axis, amp=0.01, u=(0.003, -0.002, 0.001))
     got, ref = run_pair(wl, prec, f0, 30)
     fluid = wl.solid == 0
-    assert velocity_error(wl, got, ref) <= TOL[prec]
+    assert velocity_error(wl, got, ref) <= tol(f"pillar{axis}", prec)
     if prec == "f64":
         assert np.abs(got - ref)[:, fluid].max() / np.abs(ref).max() <= 1e-12
     start = decode(encode(f0, prec), prec)
@@ -209,6 +216,6 @@ def test_classified_sphere_matches_oracle(prec):
     f0 = noisy_state((19, wl.nz, wl.ny, wl.nx), 90, amp=0.005)
     got, ref = run_pair(wl, prec, f0, 40)
     fluid = solid == 0
-    assert velocity_error(wl, got, ref) <= TOL[prec]
+    assert velocity_error(wl, got, ref) <= tol("sphere", prec)
     if prec == "f64":
         assert np.abs(got - ref)[:, fluid].max() / np.abs(ref).max() <= 1e-12

@@ -4,9 +4,9 @@ seeded inputs, element by element, plus invariants at the benchmark's full size.
 Tolerances (max over all nodes):
   f64  populations and velocity within 1e-12 relative;
   f32  velocity within 1e-5 of the largest velocity magnitude;
-  f16  (binary16 storage of f - w rho0) velocity within F16_TOL of the largest
-       velocity magnitude for the step counts used here (measured value recorded in
-       the design notes).
+  f16  (binary16 storage of f - w rho0) velocity within F16_TOL[case] of the largest
+       velocity magnitude: about twice the error measured for each case at the step
+       counts used here, so that a regression of the binary16 path shows.
 """
 import numpy as np
 import pytest
@@ -17,8 +17,17 @@ from lbm_testlib import (decode, encode, noisy_state, population_error, run_pair
 
 pytestmark = pytest.mark.gpu
 
-F16_TOL = 5e-3
-TOL = {"f64": 1e-12, "f32": 1e-5, "f16": F16_TOL}
+TOL = {"f64": 1e-12, "f32": 1e-5}
+# measured (GB300): couette 2.8e-4, duct_ragged 3.0e-4, channel_ragged 3.9e-4,
+# random_walls 1.9e-4, random_xper 3.4e-4, random_zper 2.0e-4, periodic 4.7e-4,
+# minimum_3x3x3 2.4e-4, pressure_duct_ragged 2.6e-4, pressure_random 1.6e-4,
+# pressure_random_yper 2.0e-4
+F16_TOL = {"couette": 6e-4, "duct_ragged": 6e-4, "channel_ragged": 8e-4, "random_walls": 4e-4,
+           "random_xper": 7e-4, "random_zper": 4e-4, "periodic": 1e-3, "minimum_3x3x3": 5e-4,
+           "pressure_duct_ragged": 6e-4, "pressure_random": 4e-4, "pressure_random_yper": 4e-4}
+# binary16 storage in the 5000-step Couette flow from rest (measured 1.38e-2): the
+# slow diffusive transient integrates the storage rounding
+F16_COUETTE_5000_TOL = 2.5e-2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -72,9 +81,28 @@ def test_parity_with_oracle(name, prec):
     f0 = noisy_state((19, wl.nz, wl.ny, wl.nx), seed=100 + CASES.index(name), amp=0.02, u=(0.01, -0.005, 0.008))
     got, ref = run_pair(wl, prec, f0, steps)
     ev = velocity_error(wl, got, ref)
-    assert ev <= TOL[prec], f"{name} {prec}: velocity error {ev:.3e}"
+    tol = F16_TOL[name] if prec == "f16" else TOL[prec]
+    assert ev <= tol, f"{name} {prec}: velocity error {ev:.3e}"
     if prec == "f64":
         assert population_error(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_couette_5000_steps_against_oracle(prec):
+    # BASELINE configuration 1 as stated: 5000 steps from rest, velocity error against
+    # the oracle's run in units of the wall speed
+    import oracle
+    import paper_0811_4593_gb300 as lbm
+    wl = inp.couette()
+    olat = oracle.Lattice.from_workload(wl)
+    ref = oracle.run(olat, oracle.init_equilibrium(olat), wl.steps)
+    _, uo = oracle.macros(olat, ref)
+    with lbm.Lattice.from_workload(wl, prec) as lat:
+        lat.step(wl.steps)
+        _, u = lat.macros()
+        u = u.double().cpu().numpy()
+    err = np.abs(u - uo).max() / np.abs(uo).max()
+    assert err <= {"f64": 1e-12, "f32": 1e-5, "f16": F16_COUETTE_5000_TOL}[prec], err
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
@@ -160,6 +188,64 @@ def test_residual_and_mass_match_oracle(prec):
     r_ref = np.sqrt(red_b[1]) / np.sqrt(red_b[2])
     assert abs(r2 - r_ref) / r_ref < (1e-9 if prec == "f64" else 2e-3)
     assert r3 < 1e-5 and abs(m3 - m2) / m2 < rtol  # same state: snapshot just taken
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_state_residual_matches_oracle_reduce(prec):
+    # lbm_residual on two stored states in a row: its mass and residual equal the
+    # oracle's reduction of the same decoded populations, with u_prev the oracle's
+    # velocities of the first state (so only the reduction is compared, not a run)
+    import oracle
+    import paper_0811_4593_gb300 as lbm
+    wl = inp.duct(37, 19, 23, 0.8, 0.05, 30.0)   # 16,169 nodes: 64 blocks, ragged tail
+    olat = oracle.Lattice.from_workload(wl)
+    shape = (19, wl.nz, wl.ny, wl.nx)
+    s0 = encode(noisy_state(shape, 61, u=(0.02, 0.01, 0.0)), prec)
+    s1 = encode(noisy_state(shape, 62, u=(0.015, 0.012, -0.004)), prec)
+    rtol = 1e-12 if prec == "f64" else 1e-5
+    with lbm.Lattice.from_workload(wl, prec) as lat:
+        lat.set_populations(s0)
+        r0, m0 = lat.residual()
+        lat.set_populations(s1)
+        r1, m1 = lat.residual()
+    f0, f1 = decode(s0, prec), decode(s1, prec)
+    red0 = oracle.reduce(olat, f0, None)
+    _, u0 = oracle.macros(olat, f0)
+    red1 = oracle.reduce(olat, f1, u0)
+    # the residual is a velocity difference in units of the velocity magnitude, so its
+    # bar is absolute
+    assert r0 == pytest.approx(np.sqrt(red0[1]) / np.sqrt(red0[2]), abs=1e-12)
+    assert m0 == pytest.approx(red0[0], rel=rtol)
+    assert abs(r1 - np.sqrt(red1[1]) / np.sqrt(red1[2])) <= rtol
+    assert m1 == pytest.approx(red1[0], rel=rtol)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_fused_residual_matches_oracle_reduce(prec):
+    # lbm_step_residual reduces inside the sweep; its sums equal the oracle's reduction
+    # of the state the step stored, with u_prev the oracle's velocities of the state
+    # of the previous residual step. Binary16 rounds the stored state after the
+    # reduction has seen the unrounded values, so its bar is wider.
+    import oracle
+    import paper_0811_4593_gb300 as lbm
+    wl = inp.duct(37, 19, 23, 0.8, 0.05, 30.0)
+    olat = oracle.Lattice.from_workload(wl)
+    s0 = encode(noisy_state((19, wl.nz, wl.ny, wl.nx), 63, u=(0.02, 0.01, 0.0)), prec)
+    with lbm.Lattice.from_workload(wl, prec) as lat:
+        lat.set_populations(s0)
+        r1, m1 = lat.step_residual(10)
+        a = decode(lat.get_populations(), prec)
+        r2, m2 = lat.step_residual(10)
+        b = decode(lat.get_populations(), prec)
+    _, ua = oracle.macros(olat, a)
+    red_a = oracle.reduce(olat, a, None)
+    red_b = oracle.reduce(olat, b, ua)
+    rtol_m = 1e-12 if prec == "f64" else 1e-5
+    bar_r = {"f64": 1e-12, "f32": 1e-5, "f16": 1e-3}[prec]   # absolute, in units of |u|
+    assert r1 == pytest.approx(1.0, abs=1e-12)
+    assert m1 == pytest.approx(red_a[0], rel=rtol_m)
+    assert m2 == pytest.approx(red_b[0], rel=rtol_m)
+    assert abs(r2 - np.sqrt(red_b[1]) / np.sqrt(red_b[2])) <= bar_r
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
