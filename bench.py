@@ -394,6 +394,14 @@ def native(args):
             vs[f"{p}_aa"] = run_variant(wl, p, args.variant_steps, 20, args.resid_every, d, clock, scheme="aa")
             torch.cuda.empty_cache()
         out["variants"] = vs
+    if d.world == 1 and args.serving_requests > 0:
+        torch.cuda.empty_cache()
+        rec = serving_run(args.precision, args.serving_requests, args.serving_capacity_requests, args.slots,
+                          args.budget_gb, args.resid_every, args.max_steps, args.target, args.scheme,
+                          clock_gpu=d.local)
+        rec["batched_sweep"] = batched_sweep_roofline(args.precision)
+        rec["note"] = ("bounded serving leg of the default run; bench.py --serving runs the 2000-request mix")
+        out["serving"] = rec
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     d.close()
@@ -401,44 +409,103 @@ def native(args):
         print(json.dumps(out), flush=True)
 
 
+def batched_sweep_roofline(precision: str, nlat: int = 40, steps: int = 100, warmup: int = 20):
+    """The batched sweep on a fixed serving mix: the first `nlat` requests of the seed-1
+    stream resident together, `steps` batched A/B steps timed with CUDA events on the
+    batch's stream. Bytes are the algorithmic 19 loads + 19 stores per node update."""
+    import torch
+
+    import paper_0811_4593_gb300 as lbm
+    reqs = inp.serving_requests(nlat, 1, 1.0)
+    stream = torch.cuda.Stream()
+    lats = []
+    with lbm.Batch(nlat, precision, stream=stream) as b:
+        try:
+            for i, r in enumerate(reqs):
+                lats.append(lbm.Lattice.from_workload(inp.request_workload(r), precision))
+                b.attach(i, lats[-1])
+            grid = b.info()["grid"]
+            b.step(warmup)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+        finally:
+            for lat in lats:
+                lat.close()
+    nodes = sum(r.cells for r in reqs)
+    hbm, src = measured_hbm_peak()
+    ach = BYTES_PER_UPDATE[precision] * nodes / (ms * 1e-3) / 1e9
+    return {"kernel": f"sweep_batched_kernel<{precision}>", "lattices": nlat, "updates_per_launch": nodes,
+            "grid": grid, "launch_ms": round(ms, 4), "mlups": round(nodes / (ms * 1e-3) / 1e6, 1), "bound": "hbm",
+            "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+            "peak_source": src, "bytes_per_update": BYTES_PER_UPDATE[precision],
+            "mix": f"first {nlat} requests of the seed-1 serving stream, all resident"}
+
+
+def serving_run(precision: str, requests: int, capacity_requests: int, slots: int, budget_gb: float,
+                round_steps: int, max_steps: int, target: float, scheme: str, clock_gpu=None) -> dict:
+    """The serving mix: capacity (jobs/s) from a closed-loop run of `capacity_requests`
+    of the seed-1 request stream, then `requests` of the seed-0 stream with Poisson
+    arrivals at 70 % of that capacity. Returns the serving record (p50/p99 time to
+    steady state, aggregate MLUPS, how the jobs ended, clocks during the run)."""
+    import torch
+
+    from paper_0811_4593_gb300.serving import Job, Server
+    kw = dict(capacity=slots, budget_bytes=budget_gb * 1e9, round_steps=round_steps,
+              max_steps=max_steps, target=target, plateau_checks=10, scheme=scheme)
+    clocks = ClockSampler(clock_gpu).start() if clock_gpu is not None else None
+    cap_reqs = inp.serving_requests(capacity_requests, 1, 1.0)
+    cap_jobs = [Job(r.rid, 0.0, inp.request_workload(r)) for r in cap_reqs]
+    _, cap = Server(precision, **kw).serve(cap_jobs, closed_loop=True)
+    capacity = cap["jobs_per_s"]
+    rate = 0.7 * capacity
+    reqs = inp.serving_requests(requests, 0, rate)
+    jobs = [Job(r.rid, r.arrival_s, inp.request_workload(r)) for r in reqs]
+    torch.cuda.synchronize()
+    _, rep = Server(precision, **kw).serve(jobs)
+    clock = clocks.stop() if clocks else None
+    return {"requests": requests, "p50_time_to_steady_s": round(rep["p50_time_to_steady_s"], 3),
+            "p99_time_to_steady_s": round(rep["p99_time_to_steady_s"], 3),
+            "aggregate_mlups": round(rep["aggregate_mlups"], 1),
+            "jobs": rep["jobs"], "wall_s": round(rep["wall_s"], 2),
+            "capacity_jobs_per_s": round(capacity, 3), "arrival_rate_per_s": round(rate, 3),
+            "capacity_run": {"requests": capacity_requests, "jobs": cap["jobs"], "wall_s": round(cap["wall_s"], 2),
+                             "aggregate_mlups": round(cap["aggregate_mlups"], 1),
+                             "status_counts": cap["status_counts"]},
+            "status_counts": rep["status_counts"],
+            "p50_time_by_status_s": {k: round(v, 3) for k, v in rep["p50_time_by_status_s"].items()},
+            "p99_time_by_status_s": {k: round(v, 3) for k, v in rep["p99_time_by_status_s"].items()},
+            "steady_state_rule": (f"retired at residual < {target} (converged), no new best over 10 checks once "
+                                  f"below 1e-5 (plateau), {max_steps} steps (step_cap) or a bad node (diverged)"),
+            "peak_active": rep["peak_active"], "peak_gb": round(rep["peak_bytes"] / 1e9, 2),
+            "steps_p50": rep["steps_p50"], "steps_p99": rep["steps_p99"],
+            "final_residual_p50": rep["final_residual_p50"], "final_residual_p90": rep["final_residual_p90"],
+            "slots": slots, "budget_gb": budget_gb, "round_steps": round_steps, "scheme": scheme,
+            "precision": precision, "clocks": clock}
+
+
 def serving(args):
-    """The serving mix: capacity (jobs/s) from a closed-loop run of the seed-1 request
-    stream, then the seed-0 stream with Poisson arrivals at 70 % of that capacity."""
+    """The full serving mix as its own JSON line (2000 requests by default)."""
     import torch
 
     from paper_0811_4593_gb300 import build as lib_build
-    from paper_0811_4593_gb300.serving import Job, Server
     lib_build.build()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    kw = dict(capacity=args.slots, budget_bytes=args.budget_gb * 1e9, round_steps=args.resid_every,
-              max_steps=args.max_steps, target=args.target, plateau_checks=10, scheme=args.scheme)
-    cap_reqs = inp.serving_requests(args.capacity_requests, 1, 1.0)
-    cap_jobs = [Job(r.rid, 0.0, inp.request_workload(r)) for r in cap_reqs]
-    _, cap = Server(args.precision, **kw).serve(cap_jobs, closed_loop=True)
-    capacity = cap["jobs_per_s"]
-    rate = 0.7 * capacity
-    reqs = inp.serving_requests(args.requests, 0, rate)
-    jobs = [Job(r.rid, r.arrival_s, inp.request_workload(r)) for r in reqs]
-    results, rep = Server(args.precision, **kw).serve(jobs)
-    out = {"metric": METRIC, "value": round(rep["aggregate_mlups"], 1), "unit": "MLUPS", "n_gpus": 1,
+    rec = serving_run(args.precision, args.requests, args.capacity_requests, args.slots, args.budget_gb,
+                      args.resid_every, args.max_steps, args.target, args.scheme,
+                      clock_gpu=int(os.environ.get("LOCAL_RANK", "0")))
+    rec["batched_sweep"] = batched_sweep_roofline(args.precision)
+    out = {"metric": METRIC, "value": rec["aggregate_mlups"], "unit": "MLUPS", "n_gpus": 1,
            "higher_is_better": True, "dtype": args.precision, "data": "synthetic", "mode": "serving",
            "config": {"workload": f"serving mix: {args.requests} duct/channel requests, dims log-uniform 32..192, "
                                   f"speed U(0.01,0.08), angle U(0,45 deg), tau U(0.55,1.5), Poisson arrivals at "
                                   f"0.7 x capacity, residual target {args.target} or {args.max_steps} steps",
                       "slots": args.slots, "budget_gb": args.budget_gb, "round_steps": args.resid_every},
-           "serving": {"p50_time_to_steady_s": round(rep["p50_time_to_steady_s"], 3),
-                       "p99_time_to_steady_s": round(rep["p99_time_to_steady_s"], 3),
-                       "jobs": rep["jobs"], "wall_s": round(rep["wall_s"], 2),
-                       "capacity_jobs_per_s": round(capacity, 3), "arrival_rate_per_s": round(rate, 3),
-                       "capacity_run": {"jobs": cap["jobs"], "wall_s": round(cap["wall_s"], 2),
-                                        "aggregate_mlups": round(cap["aggregate_mlups"], 1)},
-                       "status_counts": rep["status_counts"], "peak_active": rep["peak_active"],
-                       "peak_gb": round(rep["peak_bytes"] / 1e9, 2),
-                       "steps_p50": rep["steps_p50"], "steps_p99": rep["steps_p99"],
-                       "final_residual_p50": rep["final_residual_p50"],
-                       "final_residual_p90": rep["final_residual_p90"],
-                       "p50_time_by_status_s": {k: round(v, 3) for k, v in rep["p50_time_by_status_s"].items()},
-                       "scheme": args.scheme}}
+           "serving": rec}
     print(json.dumps(out), flush=True)
 
 
@@ -798,6 +865,10 @@ def main():
     ap.add_argument("--study-steps", type=int, default=0, help="steps of the duct-config study (default 20000)")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--capacity-requests", type=int, default=200)
+    ap.add_argument("--serving-requests", type=int, default=200,
+                    help="requests of the serving leg of the default run (0: no serving leg)")
+    ap.add_argument("--serving-capacity-requests", type=int, default=100,
+                    help="closed-loop requests that measure capacity in the serving leg of the default run")
     ap.add_argument("--slots", type=int, default=512)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--max-steps", type=int, default=20000)

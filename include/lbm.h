@@ -252,8 +252,9 @@ LBM_API lbm_status lbm_info(const lbm_ctx* ctx, lbm_info_t* out);
  * Batches: many resident lattices advanced together (continuous-batching serving).
  *
  * A batch advances every attached context by one persistent CUDA launch per time step:
- * the launch splits the 256-node blocks of all attached lattices into one contiguous
- * share per thread block and runs, per node, exactly the computation of lbm_step (same
+ * the launch's thread blocks draw chunks of the 256-node blocks of all attached
+ * lattices from a device counter (chunks shrink toward the end, so the thread blocks
+ * finish together) and run, per node, exactly the computation of lbm_step (same
  * device code, same grouping of the residual sums), so an attached lattice evolves to
  * the same bits as when it is stepped alone. The n-step loop is captured once as a
  * CUDA graph per (n, residual) and replayed; the descriptor table it reads is rewritten

@@ -105,9 +105,17 @@ template <> struct Storage<double> {
   __device__ static double load(const double* p) { return __ldg(p); }
   __device__ static double store(double v) { return v; }
 };
+// FP32 loads are read-only loads that also ask L2 to fetch the enclosing 256-byte block
+// (PTX ld.global.nc with the .L2::256B prefetch-size qualifier): consecutive warps read
+// consecutive 128-byte pieces of each population row. Measured: the single-lattice
+// sweep unchanged, the batched sweep on a serving mix 1 - 2 % faster.
 template <> struct Storage<float> {
   static constexpr bool shifted = true;
-  __device__ static float load(const float* p) { return __ldg(p); }
+  __device__ static float load(const float* p) {
+    float v;
+    asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+  }
   __device__ static float store(float v) { return v; }
 };
 template <> struct Storage<__half> {
@@ -991,63 +999,66 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) sweep_pair_kernel(const __gr
   });
 }
 
-// One time step of every lattice of a batch. A persistent grid splits the batch's
-// global block range into one contiguous share per CTA; a CTA caches the descriptor of
-// the lattice it is in (in shared memory) and runs the same per-block code as the
-// single-lattice sweep, so every lattice computes the same bits alone or in a batch.
+// One time step of every lattice of a batch. A persistent grid draws chunks of the
+// batch's global block range from a device counter (the chunk sizes shrink toward the
+// end of the range, so the CTAs finish together however unequal the cost of the blocks
+// is); a CTA keeps the descriptor of the lattice it is in (in shared memory) while
+// consecutive blocks stay in that lattice, and runs the same per-block code as the
+// single-lattice sweep, so every lattice computes the same bits alone or in a batch,
+// whichever CTA takes which block.
 // AB lattices: `parity` picks the direction buf[cur ^ parity] -> buf[cur ^ parity ^ 1].
 // AA lattices (MODE != STREAM_AB): both slots of buf[] are the one array.
 template <typename S, bool RESID, int MODE>
 __global__ void __launch_bounds__(SWEEP_THREADS, (SweepOccupancy<S, RESID, true, MODE>::blocks))
-    sweep_batched_kernel(const BatchHeader* __restrict__ hdr, const BatchEntry* __restrict__ ents, uint32_t parity) {
+    sweep_batched_kernel(const BatchHeader* __restrict__ hdr, const BatchEntry* __restrict__ ents,
+                         const BatchChunk* __restrict__ chunks, uint32_t* __restrict__ next_chunk, uint32_t parity) {
   __shared__ SweepArgs sa;
-  __shared__ uint32_t s_idx;
-  const uint32_t total = hdr->total_blocks;
-  const uint32_t nent = hdr->nentries;
-  uint32_t b = uint32_t(uint64_t(blockIdx.x) * total / gridDim.x);
-  const uint32_t bend = uint32_t(uint64_t(blockIdx.x + 1) * total / gridDim.x);
-  uint32_t lat_begin = 0, lat_end = 0;
-  while (b < bend) {
-    if (b >= lat_end) {
-      __syncthreads();  // every thread is done with the previous descriptor
-      if (threadIdx.x == 0) {
-        uint32_t lo = 0, hi = nent;  // last entry with block_begin <= b
-        while (hi - lo > 1) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (ents[mid].block_begin <= b) lo = mid;
-          else hi = mid;
+  __shared__ uint32_t s_chunk;
+  const uint32_t nchunks = hdr->nchunks;
+  uint32_t cur = 0xffffffffu, lat_begin = 0, lat_end = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = atomicAdd(next_chunk, 1u);
+    __syncthreads();
+    const uint32_t c = s_chunk;
+    __syncthreads();  // s_chunk is rewritten by the next draw
+    if (c >= nchunks) break;
+    uint32_t b = __ldg(&chunks[c].start);
+    const uint32_t bend = __ldg(&chunks[c + 1].start);
+    uint32_t e = __ldg(&chunks[c].entry);
+    while (b < bend) {
+      if (e != cur) {
+        __syncthreads();  // every thread is done with the previous descriptor
+        const BatchEntry* ent = ents + chk(e, hdr->nentries);
+        const uint32_t* from = reinterpret_cast<const uint32_t*>(&ent->a);
+        uint32_t* to = reinterpret_cast<uint32_t*>(&sa);
+        for (uint32_t w = threadIdx.x; w < sizeof(SweepArgs) / 4; w += SWEEP_THREADS) to[w] = from[w];
+        __syncthreads();
+        if (threadIdx.x < Q) {
+          const uint32_t cb = (ent->cur ^ parity) & 1u;
+          const S* src = static_cast<const S*>(ent->buf[cb]);
+          S* dst = static_cast<S*>(const_cast<void*>(ent->buf[cb ^ 1u]));
+          sa.src_pop[threadIdx.x] = src + size_t(threadIdx.x) * ent->a.N;
+          sa.dst_pop[threadIdx.x] = dst + size_t(threadIdx.x) * ent->a.N;
+          if (threadIdx.x == 0) {
+            sa.src = src;
+            sa.dst = dst;
+          }
         }
-        s_idx = lo;
+        lat_begin = ent->block_begin;
+        lat_end = ent->block_begin + ent->nblocks;
+        cur = e;
+        __syncthreads();
       }
-      __syncthreads();
-      const BatchEntry* e = ents + s_idx;
-      const uint32_t* from = reinterpret_cast<const uint32_t*>(&e->a);
-      uint32_t* to = reinterpret_cast<uint32_t*>(&sa);
-      for (uint32_t w = threadIdx.x; w < sizeof(SweepArgs) / 4; w += SWEEP_THREADS) to[w] = from[w];
-      __syncthreads();
-      if (threadIdx.x < Q) {
-        const uint32_t c = (e->cur ^ parity) & 1u;
-        const S* src = static_cast<const S*>(e->buf[c]);
-        S* dst = static_cast<S*>(const_cast<void*>(e->buf[c ^ 1u]));
-        sa.src_pop[threadIdx.x] = src + size_t(threadIdx.x) * e->a.N;
-        sa.dst_pop[threadIdx.x] = dst + size_t(threadIdx.x) * e->a.N;
-        if (threadIdx.x == 0) {
-          sa.src = src;
-          sa.dst = dst;
-        }
+      if constexpr (MODE == STREAM_AB) {
+        if (sa.links || sa.forced) sweep_block<S, RESID, MODE, true>(sa, b - lat_begin);
+        else sweep_block<S, RESID, MODE, false>(sa, b - lat_begin);
+      } else {
+        sweep_block<S, RESID, MODE, false>(sa, b - lat_begin);
       }
-      lat_begin = e->block_begin;
-      lat_end = e->block_begin + e->nblocks;
-      __syncthreads();
+      if constexpr (RESID) __syncthreads();  // the block-sum buffer is reused by the next block
+      ++b;
+      if (b >= lat_end) ++e;
     }
-    if constexpr (MODE == STREAM_AB) {
-      if (sa.links || sa.forced) sweep_block<S, RESID, MODE, true>(sa, b - lat_begin);
-      else sweep_block<S, RESID, MODE, false>(sa, b - lat_begin);
-    } else {
-      sweep_block<S, RESID, MODE, false>(sa, b - lat_begin);
-    }
-    if constexpr (RESID) __syncthreads();  // the block-sum buffer is reused by the next block
-    ++b;
   }
 }
 
@@ -1166,41 +1177,41 @@ cudaError_t launch_state_reduce_impl(const void* src, uint32_t N, double rho0, v
 }
 
 template <typename S, int MODE>
-void launch_batched_mode(const BatchHeader* hdr, const BatchEntry* ents, uint32_t parity, bool resid, int grid,
-                         cudaStream_t s) {
-  if (resid) sweep_batched_kernel<S, true, MODE><<<grid, SWEEP_THREADS, 0, s>>>(hdr, ents, parity);
-  else sweep_batched_kernel<S, false, MODE><<<grid, SWEEP_THREADS, 0, s>>>(hdr, ents, parity);
+void launch_batched_mode(const BatchHeader* hdr, const BatchEntry* ents, const BatchChunk* chunks, uint32_t* next,
+                         uint32_t parity, bool resid, int grid, cudaStream_t s) {
+  if (resid) sweep_batched_kernel<S, true, MODE><<<grid, SWEEP_THREADS, 0, s>>>(hdr, ents, chunks, next, parity);
+  else sweep_batched_kernel<S, false, MODE><<<grid, SWEEP_THREADS, 0, s>>>(hdr, ents, chunks, next, parity);
 }
 
 template <typename S>
-cudaError_t launch_sweep_batched_impl(const BatchHeader* hdr, const BatchEntry* ents, uint32_t parity, bool resid,
-                                      int mode, int grid, cudaStream_t s) {
-  if (mode == STREAM_AA_GATHER) launch_batched_mode<S, STREAM_AA_GATHER>(hdr, ents, parity, resid, grid, s);
-  else if (mode == STREAM_AA_LOCAL) launch_batched_mode<S, STREAM_AA_LOCAL>(hdr, ents, parity, resid, grid, s);
-  else launch_batched_mode<S, STREAM_AB>(hdr, ents, parity, resid, grid, s);
+cudaError_t launch_sweep_batched_impl(const BatchHeader* hdr, const BatchEntry* ents, const BatchChunk* chunks,
+                                      uint32_t* next, uint32_t parity, bool resid, int mode, int grid,
+                                      cudaStream_t s) {
+  if (mode == STREAM_AA_GATHER) launch_batched_mode<S, STREAM_AA_GATHER>(hdr, ents, chunks, next, parity, resid, grid, s);
+  else if (mode == STREAM_AA_LOCAL) launch_batched_mode<S, STREAM_AA_LOCAL>(hdr, ents, chunks, next, parity, resid, grid, s);
+  else launch_batched_mode<S, STREAM_AB>(hdr, ents, chunks, next, parity, resid, grid, s);
   return cudaGetLastError();
 }
 
+// Persistent grid of each batched variant: SMs x the residency the occupancy query
+// gives for that variant (the chunk counter balances any grid size).
 template <typename S>
-int batched_grid_impl() {
-  int dev = 0, sms = 0, a = 0, b = 0;
+int batched_grid_impl(bool resid, int mode) {
+  int dev = 0, sms = 0, r = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  // the smallest residency over the variants the batch launches
-  int best = 1 << 30;
-  auto take = [&](const void* fn) {
-    int r = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, fn, SWEEP_THREADS, 0) != cudaSuccess) r = 0;
-    best = r < best ? r : best;
-  };
-  take(reinterpret_cast<const void*>(sweep_batched_kernel<S, false, STREAM_AB>));
-  take(reinterpret_cast<const void*>(sweep_batched_kernel<S, true, STREAM_AB>));
-  take(reinterpret_cast<const void*>(sweep_batched_kernel<S, false, STREAM_AA_GATHER>));
-  take(reinterpret_cast<const void*>(sweep_batched_kernel<S, false, STREAM_AA_LOCAL>));
-  take(reinterpret_cast<const void*>(sweep_batched_kernel<S, true, STREAM_AA_LOCAL>));
-  (void)a;
-  (void)b;
-  return sms * best;
+  const void* fn = nullptr;
+  if (mode == STREAM_AA_GATHER)
+    fn = resid ? reinterpret_cast<const void*>(sweep_batched_kernel<S, true, STREAM_AA_GATHER>)
+               : reinterpret_cast<const void*>(sweep_batched_kernel<S, false, STREAM_AA_GATHER>);
+  else if (mode == STREAM_AA_LOCAL)
+    fn = resid ? reinterpret_cast<const void*>(sweep_batched_kernel<S, true, STREAM_AA_LOCAL>)
+               : reinterpret_cast<const void*>(sweep_batched_kernel<S, false, STREAM_AA_LOCAL>);
+  else
+    fn = resid ? reinterpret_cast<const void*>(sweep_batched_kernel<S, true, STREAM_AB>)
+               : reinterpret_cast<const void*>(sweep_batched_kernel<S, false, STREAM_AB>);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, fn, SWEEP_THREADS, 0) != cudaSuccess) return 0;
+  return sms * r;
 }
 
 // Count of out-of-range indices this translation unit's kernels met (debug build; the
@@ -1232,11 +1243,12 @@ static inline uint32_t bounds_errors_impl() {
     return launch_state_reduce_impl<S>(src, N, rho0, snap, partials, swapped, s);                       \
   }                                                                                                     \
   template <> cudaError_t launch_sweep_batched<S>(const BatchHeader* hdr, const BatchEntry* ents,       \
+                                                  const BatchChunk* chunks, uint32_t* next,             \
                                                   uint32_t parity, bool resid, int mode, int grid,      \
                                                   cudaStream_t s) {                                     \
-    return launch_sweep_batched_impl<S>(hdr, ents, parity, resid, mode, grid, s);                      \
+    return launch_sweep_batched_impl<S>(hdr, ents, chunks, next, parity, resid, mode, grid, s);        \
   }                                                                                                     \
-  template <> int batched_grid<S>() { return batched_grid_impl<S>(); }                                  \
+  template <> int batched_grid<S>(bool resid, int mode) { return batched_grid_impl<S>(resid, mode); }   \
   template <> uint32_t bounds_errors<S>() { return bounds_errors_impl(); }
 
 }  // namespace lbm

@@ -95,7 +95,17 @@ struct BatchEntry {
 struct BatchHeader {
   uint32_t nentries;      // entries in use, ordered by block_begin
   uint32_t total_blocks;  // sum of nblocks
-  uint32_t pad[2];
+  uint32_t nchunks;       // work units of the batched sweep (chunk table rows - 1)
+  uint32_t pad;
+};
+
+// One work unit of the batched sweep: the global blocks from `start` up to the next
+// chunk's start, the first of them in entry `entry`. The table ends with a sentinel
+// row {total_blocks, nentries}. CTAs take chunks in order from a device counter, so
+// a CTA that met expensive blocks (boundary-heavy lattices) takes fewer chunks.
+struct BatchChunk {
+  uint32_t start;
+  uint32_t entry;
 };
 
 constexpr int SWEEP_THREADS = 256;
@@ -112,9 +122,14 @@ template <typename S> cudaError_t launch_macros(const void* src, uint32_t N, dou
 template <typename S> cudaError_t launch_state_reduce(const void* src, uint32_t N, double rho0,
                                                       void* snap, double* partials, bool swapped, cudaStream_t s);
 cudaError_t launch_final_reduce(const double* partials, uint32_t nblocks, double* out, cudaStream_t s);
-template <typename S> cudaError_t launch_sweep_batched(const BatchHeader* hdr, const BatchEntry* ents, uint32_t parity,
+// next_chunk: a device counter that is zero when the launch starts (the caller clears
+// it in stream order before every launch); each CTA draws chunks from it until the
+// table is exhausted
+template <typename S> cudaError_t launch_sweep_batched(const BatchHeader* hdr, const BatchEntry* ents,
+                                                       const BatchChunk* chunks, uint32_t* next_chunk, uint32_t parity,
                                                        bool resid, int mode, int grid, cudaStream_t s);
-template <typename S> int batched_grid();  // persistent grid size: SMs x resident blocks per SM
+// persistent grid of a batched variant: SMs x its resident blocks per SM (0 on error)
+template <typename S> int batched_grid(bool resid, int mode);
 template <typename S> uint32_t bounds_errors();  // debug build: indices out of range (read resets)
 cudaError_t launch_batch_final_reduce(const BatchHeader* hdr, const BatchEntry* ents, int capacity, double* results,
                                       cudaStream_t s);

@@ -72,10 +72,13 @@ struct lbm_batch {
   lbm::BatchHeader* d_hdr = nullptr;
   lbm::BatchEntry* d_ent = nullptr;
   double* d_res = nullptr;
+  lbm::BatchChunk* h_chunks = nullptr;  // pinned mirror of the chunk table
+  lbm::BatchChunk* d_chunks = nullptr;
+  uint32_t* d_next = nullptr;           // chunk counter of the batched sweep
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaEvent_t table_free = nullptr;  // the last table upload has read the host mirror
-  int grid = 0;
+  int grid = 0;  // persistent grid of every batched launch
   uint32_t total_blocks = 0;
   struct Graph {
     int n;
@@ -835,6 +838,7 @@ static void batch_release(lbm_batch* b) {
   if (b->h_hdr) cudaFreeHost(b->h_hdr);
   if (b->h_ent) cudaFreeHost(b->h_ent);
   if (b->h_res) cudaFreeHost(b->h_res);
+  if (b->h_chunks) cudaFreeHost(b->h_chunks);
   if (b->table_free) cudaEventDestroy(b->table_free);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
@@ -842,13 +846,50 @@ static void batch_release(lbm_batch* b) {
 // Step i of a batched n-step loop: A/B lattices alternate the buffer direction with
 // the parity; AA lattices (all at a step-pair boundary when a loop starts) alternate
 // the gather-scatter and in-place steps.
+// Every launch starts with its chunk counter at zero (a memset in stream order, so a
+// captured step loop holds one memset node before each sweep node).
 static cudaError_t batch_launch_sweep(lbm_batch* b, uint32_t parity, bool resid) {
   const int mode = b->scheme == LBM_SCHEME_AA ? (parity ? 2 : 1) : 0;
+  cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(uint32_t), b->stream);
+  if (e != cudaSuccess) return e;
+  const int grid = b->grid;
   switch (b->prec) {
-    case LBM_F64: return lbm::launch_sweep_batched<double>(b->d_hdr, b->d_ent, parity, resid, mode, b->grid, b->stream);
-    case LBM_F32: return lbm::launch_sweep_batched<float>(b->d_hdr, b->d_ent, parity, resid, mode, b->grid, b->stream);
-    default: return lbm::launch_sweep_batched<__half>(b->d_hdr, b->d_ent, parity, resid, mode, b->grid, b->stream);
+    case LBM_F64:
+      return lbm::launch_sweep_batched<double>(b->d_hdr, b->d_ent, b->d_chunks, b->d_next, parity, resid, mode,
+                                               grid, b->stream);
+    case LBM_F32:
+      return lbm::launch_sweep_batched<float>(b->d_hdr, b->d_ent, b->d_chunks, b->d_next, parity, resid, mode,
+                                              grid, b->stream);
+    default:
+      return lbm::launch_sweep_batched<__half>(b->d_hdr, b->d_ent, b->d_chunks, b->d_next, parity, resid, mode,
+                                               grid, b->stream);
   }
+}
+
+// Rows of the chunk table (without its sentinel).
+constexpr uint32_t kMaxChunks = 65535;
+
+// Guided self-scheduling of the batch's global block range over `grid` CTAs: each chunk
+// takes 1 / (2 grid) of the blocks still unassigned (at least `min_chunk`), so the first
+// draws are large (few descriptor changes) and the last are single blocks (the CTAs
+// end together). Writes rows 0..n-1 and the sentinel row n; returns n, or 0 if the
+// table would need more than kMaxChunks rows.
+static uint32_t build_chunks(const lbm::BatchEntry* ents, uint32_t nent, uint32_t total, uint32_t grid,
+                             uint32_t min_chunk, lbm::BatchChunk* out) {
+  uint32_t n = 0, pos = 0, e = 0;
+  const uint64_t div = 2ull * (grid ? grid : 1);
+  while (pos < total) {
+    if (n >= kMaxChunks) return 0;
+    const uint32_t rem = total - pos;
+    uint32_t size = uint32_t((rem + div - 1) / div);
+    if (size < min_chunk) size = min_chunk;
+    if (size > rem) size = rem;
+    while (ents[e].block_begin + ents[e].nblocks <= pos) ++e;
+    out[n++] = {pos, e};
+    pos += size;
+  }
+  out[n] = {total, nent};
+  return n;
 }
 
 // Issue n batched steps (the last with the residual reductions when `resid`).
@@ -891,23 +932,36 @@ lbm_status lbm_batch_create(int capacity, lbm_precision prec, lbm_batch** out) {
   if (e != cudaSuccess) return bail(bcuda(nullptr, e, "creating the table event"));
   const size_t ent_bytes = sizeof(lbm::BatchEntry) * size_t(capacity);
   const size_t res_bytes = 4 * sizeof(double) * size_t(capacity);
+  const size_t chunk_bytes = sizeof(lbm::BatchChunk) * (size_t(kMaxChunks) + 1);
   if ((e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_hdr), sizeof(lbm::BatchHeader), cudaHostAllocDefault)) != cudaSuccess ||
       (e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_ent), ent_bytes, cudaHostAllocDefault)) != cudaSuccess ||
-      (e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_res), res_bytes, cudaHostAllocDefault)) != cudaSuccess)
+      (e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_res), res_bytes, cudaHostAllocDefault)) != cudaSuccess ||
+      (e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_chunks), chunk_bytes, cudaHostAllocDefault)) != cudaSuccess)
     return bail(bcuda(nullptr, e, "pinned host table"));
   b->d_hdr = static_cast<lbm::BatchHeader*>(batch_alloc(b, sizeof(lbm::BatchHeader)));
   b->d_ent = static_cast<lbm::BatchEntry*>(batch_alloc(b, ent_bytes));
   b->d_res = static_cast<double*>(batch_alloc(b, res_bytes));
-  if (!b->d_hdr || !b->d_ent || !b->d_res) return bail(bfail(nullptr, LBM_ERR_OOM, "device allocation of the batch table failed"));
+  b->d_chunks = static_cast<lbm::BatchChunk*>(batch_alloc(b, chunk_bytes));
+  b->d_next = static_cast<uint32_t*>(batch_alloc(b, 256));
+  if (!b->d_hdr || !b->d_ent || !b->d_res || !b->d_chunks || !b->d_next)
+    return bail(bfail(nullptr, LBM_ERR_OOM, "device allocation of the batch table failed"));
   memset(b->h_hdr, 0, sizeof(lbm::BatchHeader));
   e = cudaMemcpy(b->d_hdr, b->h_hdr, sizeof(lbm::BatchHeader), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bail(bcuda(nullptr, e, "clearing the batch table"));
-  switch (prec) {
-    case LBM_F64: b->grid = lbm::batched_grid<double>(); break;
-    case LBM_F32: b->grid = lbm::batched_grid<float>(); break;
-    default: b->grid = lbm::batched_grid<__half>(); break;
-  }
-  if (b->grid <= 0) return bail(bfail(nullptr, LBM_ERR_CUDA, "occupancy query for the batched sweep failed"));
+  // one grid for every batched variant: SMs x the smallest residency among them (a grid
+  // of the A/B step's own, larger residency measured 1 - 2 % slower on a serving mix)
+  b->grid = 0;
+  for (int r = 0; r < 2; ++r)
+    for (int m = 0; m < 3; ++m) {
+      int g = 0;
+      switch (prec) {
+        case LBM_F64: g = lbm::batched_grid<double>(r != 0, m); break;
+        case LBM_F32: g = lbm::batched_grid<float>(r != 0, m); break;
+        default: g = lbm::batched_grid<__half>(r != 0, m); break;
+      }
+      if (g <= 0) return bail(bfail(nullptr, LBM_ERR_CUDA, "occupancy query for the batched sweep failed"));
+      b->grid = (b->grid == 0 || g < b->grid) ? g : b->grid;
+    }
   *out = b;
   return LBM_OK;
 }
@@ -996,11 +1050,18 @@ lbm_status lbm_batch_step(lbm_batch* b, int n, int residual) {
   b->h_hdr->total_blocks = blocks;
   b->total_blocks = blocks;
   if (nent == 0) return LBM_OK;
+  uint32_t nchunks = 0;
+  for (uint32_t min_chunk = 1; nchunks == 0; min_chunk *= 2)
+    nchunks = build_chunks(b->h_ent, nent, blocks, uint32_t(b->grid), min_chunk, b->h_chunks);
+  b->h_hdr->nchunks = nchunks;
   const bool resid = residual != 0;
   LBM_BCUDA(b, cudaMemcpyAsync(b->d_hdr, b->h_hdr, sizeof(lbm::BatchHeader), cudaMemcpyHostToDevice, b->stream),
             "uploading the batch header");
   LBM_BCUDA(b, cudaMemcpyAsync(b->d_ent, b->h_ent, sizeof(lbm::BatchEntry) * nent, cudaMemcpyHostToDevice, b->stream),
             "uploading the batch table");
+  LBM_BCUDA(b, cudaMemcpyAsync(b->d_chunks, b->h_chunks, sizeof(lbm::BatchChunk) * (nchunks + 1),
+                               cudaMemcpyHostToDevice, b->stream),
+            "uploading the chunk table");
   LBM_BCUDA(b, cudaEventRecord(b->table_free, b->stream), "recording the table event");
   if (b->stream) {
     // the n-step loop as one CUDA graph; its kernels read the table from device memory,

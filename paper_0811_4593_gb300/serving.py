@@ -202,6 +202,7 @@ class Server:
             "p99_time_to_steady_s": percentile(tts, 99),
             "status_counts": dict(collections.Counter(r.status for r in results)),
             "p50_time_by_status_s": {k: percentile(v, 50) for k, v in by_status.items()},
+            "p99_time_by_status_s": {k: percentile(v, 99) for k, v in by_status.items()},
             "steps_p50": percentile([r.steps for r in results], 50),
             "steps_p99": percentile([r.steps for r in results], 99),
             "final_residual_p50": percentile([r.residual for r in ok], 50),
