@@ -42,6 +42,55 @@ __device__ __forceinline__ double op_mul(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float op_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double op_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// Two FP32 values as one operand of the packed FP32 instructions (PTX add, sub, mul and
+// fma with the .rn.f32x2 type, sm_100 and later): lane x belongs to node A of a pair,
+// lane y to node B. Every lane is one IEEE single-precision operation rounded to
+// nearest, exactly as the scalar op_* functions round, so code written once over T
+// gives the same bits per node for T = float and T = f32x2 with half the arithmetic
+// instructions for the pair.
+struct f32x2 {
+  float x, y;
+  f32x2() = default;
+  __host__ __device__ constexpr f32x2(float v) : x(v), y(v) {}
+  __host__ __device__ constexpr f32x2(double v) : x(float(v)), y(float(v)) {}
+  __host__ __device__ constexpr f32x2(int v) : x(float(v)), y(float(v)) {}
+  __host__ __device__ constexpr f32x2(float a, float b) : x(a), y(b) {}
+};
+__device__ __forceinline__ unsigned long long pk(f32x2 v) {
+  return static_cast<unsigned long long>(__float_as_uint(v.x)) |
+         (static_cast<unsigned long long>(__float_as_uint(v.y)) << 32);
+}
+__device__ __forceinline__ f32x2 upk(unsigned long long d) {
+  return f32x2(__uint_as_float(static_cast<unsigned>(d)), __uint_as_float(static_cast<unsigned>(d >> 32)));
+}
+__device__ __forceinline__ f32x2 op_add(f32x2 a, f32x2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+  return upk(d);
+}
+__device__ __forceinline__ f32x2 op_sub(f32x2 a, f32x2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+  return upk(d);
+}
+__device__ __forceinline__ f32x2 op_mul(f32x2 a, f32x2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+  return upk(d);
+}
+__device__ __forceinline__ f32x2 op_fma(f32x2 a, f32x2 b, f32x2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)), "l"(pk(c)));
+  return upk(d);
+}
+__device__ __forceinline__ f32x2 operator-(f32x2 a) { return f32x2(-a.x, -a.y); }
+// per-lane IEEE division, as the scalar a / b
+__device__ __forceinline__ f32x2 operator/(f32x2 a, f32x2 b) { return f32x2(a.x / b.x, a.y / b.y); }
+
+// The scalar type of one lane (float for f32x2).
+template <typename T> struct LaneOf { using type = T; };
+template <> struct LaneOf<f32x2> { using type = float; };
+
 // Index checks of the debug build (LBM_DEBUG_BOUNDS): an index at or beyond its limit
 // is counted in this translation unit's error word and replaced by 0, so the access
 // stays inside the buffer; lbm_debug_bounds_errors reads the count. The release build
@@ -555,6 +604,7 @@ __device__ __forceinline__ void apply_rule(uint32_t r, T (&h)[Q], double ref) {
 template <typename T>
 struct Moments {
   T drho, rho, jx, jy, jz, ux, uy, uz;  // drho = sum of v; rho = ref + drho; j = rho u
+  T inv;                                // 1 / rho
 };
 
 template <typename T>
@@ -577,6 +627,7 @@ __device__ __forceinline__ Moments<T> moments(const T (&h)[Q], T rho0) {
   m.jy = jy;
   m.jz = jz;
   const T inv = T(1) / m.rho;
+  m.inv = inv;
   m.ux = op_mul(m.jx, inv);
   m.uy = op_mul(jy, inv);
   m.uz = op_mul(jz, inv);
@@ -602,6 +653,11 @@ __device__ __forceinline__ Moments<T> moments(const T (&h)[Q], T rho0) {
 // u' = 3/2 u (omega w_i s_i = A_i (c_i.u'), b = drho - j.u'), one multiply fewer per
 // pair; the float sweeps, bound by memory, keep g_i (c_i.j)(c_i.u) with
 // g_i = 9/2 omega w_i, which measured marginally faster there.
+// The binary16 sweeps (no coefficient pair) also run on packed pairs of nodes (f32x2),
+// whose multiplies the assembler was measured to fuse with a following add or subtract
+// although both are written with round-to-nearest; so there no product feeds an add:
+// c_i.u is formed as (c_i.j) / rho, and the momentum term enters the populations through
+// fused multiply-adds, v^eq_{+-i} part = fma(+-3 omega w_i, c_i.j, t_i).
 template <bool EXACT_MOMENTUM = false, typename T>
 __device__ __forceinline__ void collide(T (&h)[Q], const Moments<T>& m, T omega,
                                         const float (*coef)[2] = nullptr) {
@@ -617,31 +673,40 @@ __device__ __forceinline__ void collide(T (&h)[Q], const Moments<T>& m, T omega,
   if constexpr (VFORM) b = op_sub(m.drho, jv);
   else b = op_fma(T(-1.5), jv, m.drho);
   const T keep = op_sub(T(1), omega);
-  const T ow_axis = op_mul(omega, wgt<T>(0)), ow_diag = op_mul(omega, wgt<T>(6));
+  using L = typename LaneOf<T>::type;
+  const T ow_axis = op_mul(omega, T(wgt<L>(0))), ow_diag = op_mul(omega, T(wgt<L>(6)));
   const T ob_axis = op_mul(ow_axis, b), ob_diag = op_mul(ow_diag, b);
   const T g_axis = op_mul(T(4.5), ow_axis), g_diag = op_mul(T(4.5), ow_diag);
   const T a_axis = op_mul(T(3), ow_axis), a_diag = op_mul(T(3), ow_diag);
+  const T na_axis = -a_axis, na_diag = -a_diag;  // exact
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     constexpr int o = opp(k);
     if constexpr (k == Q - 1) {
-      h[k] = op_fma(keep, h[k], op_mul(op_mul(omega, wgt<T>(k)), b));
+      h[k] = op_fma(keep, h[k], op_mul(op_mul(omega, T(wgt<L>(k))), b));
     } else if constexpr (k < o) {
       constexpr bool axis = w36(k) == 2;
       const T cj = dot_c<k>(m.jx, m.jy, m.jz);
-      const T cv = dot_c<k>(vx, vy, vz);
-      T a;
-      if constexpr (EXACT_MOMENTUM) {
-        const float* ab = coef[axis ? 0 : 1];
-        a = op_fma(T(ab[0]), cj, op_mul(T(ab[1]), cj));
+      if constexpr (VFORM || EXACT_MOMENTUM) {
+        const T cv = dot_c<k>(vx, vy, vz);
+        T a;
+        if constexpr (EXACT_MOMENTUM) {
+          const float* ab = coef[axis ? 0 : 1];
+          a = op_fma(T(ab[0]), cj, op_mul(T(ab[1]), cj));
+        } else {
+          a = op_mul(axis ? a_axis : a_diag, cj);
+        }
+        T t;
+        if constexpr (VFORM) t = op_fma(a, cv, axis ? ob_axis : ob_diag);
+        else t = op_fma(op_mul(axis ? g_axis : g_diag, cj), cv, axis ? ob_axis : ob_diag);
+        h[k] = op_fma(keep, h[k], op_add(t, a));
+        h[o] = op_fma(keep, h[o], op_sub(t, a));
       } else {
-        a = op_mul(axis ? a_axis : a_diag, cj);
+        const T cv = op_mul(cj, m.inv);
+        const T t = op_fma(op_mul(axis ? g_axis : g_diag, cj), cv, axis ? ob_axis : ob_diag);
+        h[k] = op_fma(keep, h[k], op_fma(axis ? a_axis : a_diag, cj, t));
+        h[o] = op_fma(keep, h[o], op_fma(axis ? na_axis : na_diag, cj, t));
       }
-      T t;
-      if constexpr (VFORM) t = op_fma(a, cv, axis ? ob_axis : ob_diag);
-      else t = op_fma(op_mul(axis ? g_axis : g_diag, cj), cv, axis ? ob_axis : ob_diag);
-      h[k] = op_fma(keep, h[k], op_add(t, a));
-      h[o] = op_fma(keep, h[o], op_sub(t, a));
     }
   });
 }
@@ -901,21 +966,35 @@ __device__ __forceinline__ void ld_half2_l2(const __half* p, float& lo, float& h
 // MODE STREAM_AA_GATHER reads slot -k of the source node instead of slot k.
 template <int MODE>
 __device__ __forceinline__ void load_pair(const SweepArgs& a, uint32_t x0, uint32_t xam, uint32_t xbp,
-                                          const uint32_t (&rows)[3][3], float (&hA)[Q], float (&hB)[Q]) {
+                                          const uint32_t (&rows)[3][3], f32x2 (&h)[Q]) {
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     constexpr int slot = MODE == STREAM_AA_GATHER ? opp(k) : k;
     const __half* base = static_cast<const __half*>(a.src_pop[slot]);
     const uint32_t row = rows[1 - cz(k)][1 - cy(k)];
     if constexpr (cx(k) == 0) {
-      ld_half2_l2(base + chk(row + x0, a.N - 1), hA[k], hB[k]);
+      ld_half2_l2(base + chk(row + x0, a.N - 1), h[k].x, h[k].y);
     } else if constexpr (cx(k) > 0) {  // pulled from x - 1
-      hB[k] = ld_half_l2(base + chk(row + x0, a.N));
-      hA[k] = ld_half_l2(base + chk(row + xam, a.N));
+      h[k].y = ld_half_l2(base + chk(row + x0, a.N));
+      h[k].x = ld_half_l2(base + chk(row + xam, a.N));
     } else {  // pulled from x + 1
-      hA[k] = ld_half_l2(base + chk(row + x0 + 1, a.N));
-      hB[k] = ld_half_l2(base + chk(row + xbp, a.N));
+      h[k].x = ld_half_l2(base + chk(row + x0 + 1, a.N));
+      h[k].y = ld_half_l2(base + chk(row + xbp, a.N));
     }
+  });
+}
+
+// Boundary closure of one node of a pair (LANE 0: node A, 1: node B) on its scalar
+// populations.
+template <int LANE>
+__device__ __forceinline__ void close_lane(int code, const SweepArgs& a, uint32_t x, uint32_t y, uint32_t z,
+                                           f32x2 (&h)[Q]) {
+  float t[Q];
+  static_for<0, Q>([&](auto kc) { t[decltype(kc)::value] = LANE ? h[decltype(kc)::value].y : h[decltype(kc)::value].x; });
+  apply_boundary(code, a, x, y, z, t);
+  static_for<0, Q>([&](auto kc) {
+    if (LANE) h[decltype(kc)::value].y = t[decltype(kc)::value];
+    else h[decltype(kc)::value].x = t[decltype(kc)::value];
   });
 }
 
@@ -949,14 +1028,14 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) sweep_pair_kernel(const __gr
   // walled axis: those populations are unknown and overwritten by the closure)
   const uint32_t xam = x0 ? x0 - 1 : (px ? a.nx - 1 : 0);
   const uint32_t xbp = (x0 + 2 < a.nx) ? x0 + 2 : (px ? 0 : a.nx - 1);
-  float hA[Q], hB[Q];
+  f32x2 h[Q];
   if constexpr (MODE == STREAM_AA_LOCAL) {
     static_for<0, Q>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
-      ld_half2_l2(static_cast<const __half*>(a.src_pop[k]) + chk(cell, a.N - 1), hA[k], hB[k]);
+      ld_half2_l2(static_cast<const __half*>(a.src_pop[k]) + chk(cell, a.N - 1), h[k].x, h[k].y);
     });
   } else {
-    load_pair<MODE>(a, x0, xam, xbp, rows, hA, hB);
+    load_pair<MODE>(a, x0, xam, xbp, rows, h);
   }
   const int fxA = px ? 0 : (x0 == 0 ? 1 : 0);
   const int fxB = px ? 0 : (x0 + 1 == a.nx - 1 ? 2 : 0);
@@ -964,20 +1043,19 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) sweep_pair_kernel(const __gr
   const int fz = pz ? 0 : (z == 0 ? 1 : (z == a.nz - 1 ? 2 : 0));
   const int codeA = fxA + 3 * fy + 9 * fz;
   const int codeB = fxB + 3 * fy + 9 * fz;
-  if (codeA != 0) apply_boundary(codeA, a, x0, y, z, hA);
-  if (codeB != 0) apply_boundary(codeB, a, x0 + 1, y, z, hB);
-  const Moments<float> mA = moments(hA, a.rho0f);
-  collide(hA, mA, a.omegaf);
-  const Moments<float> mB = moments(hB, a.rho0f);
-  collide(hB, mB, a.omegaf);
+  if (codeA != 0) close_lane<0>(codeA, a, x0, y, z, h);
+  if (codeB != 0) close_lane<1>(codeB, a, x0 + 1, y, z, h);
+  // moments and collision of both nodes at once, in packed FP32
+  const Moments<f32x2> m = moments(h, f32x2(a.rho0f));
+  collide(h, m, f32x2(a.omegaf));
   static_for<0, Q>([&](auto kc) {
     constexpr int k = decltype(kc)::value;
     if constexpr (MODE == STREAM_AB) {
       *reinterpret_cast<__half2*>(static_cast<__half*>(a.dst_pop[k]) + chk(cell, a.N - 1)) =
-          __floats2half2_rn(hA[k], hB[k]);
+          __floats2half2_rn(h[k].x, h[k].y);
     } else if constexpr (MODE == STREAM_AA_LOCAL) {
       *reinterpret_cast<__half2*>(static_cast<__half*>(a.dst_pop[opp(k)]) + chk(cell, a.N - 1)) =
-          __floats2half2_rn(hA[k], hB[k]);
+          __floats2half2_rn(h[k].x, h[k].y);
     } else {
       // push f*_k to slot k of node x + c_k; a target beyond a walled face does not exist
       const bool in_yz = !((fy == 1 && cy(k) < 0) || (fy == 2 && cy(k) > 0) || (fz == 1 && cz(k) < 0) ||
@@ -986,17 +1064,240 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) sweep_pair_kernel(const __gr
         __half* pop = static_cast<__half*>(a.dst_pop[k]);
         const uint32_t row = rows[1 + cz(k)][1 + cy(k)];
         if constexpr (cx(k) == 0) {
-          *reinterpret_cast<__half2*>(pop + chk(row + x0, a.N - 1)) = __floats2half2_rn(hA[k], hB[k]);
+          *reinterpret_cast<__half2*>(pop + chk(row + x0, a.N - 1)) = __floats2half2_rn(h[k].x, h[k].y);
         } else if constexpr (cx(k) > 0) {  // A -> x0 + 1, B -> x0 + 2
-          pop[chk(row + x0 + 1, a.N)] = __float2half_rn(hA[k]);
-          if (fxB != 2) pop[chk(row + xbp, a.N)] = __float2half_rn(hB[k]);
+          pop[chk(row + x0 + 1, a.N)] = __float2half_rn(h[k].x);
+          if (fxB != 2) pop[chk(row + xbp, a.N)] = __float2half_rn(h[k].y);
         } else {  // A -> x0 - 1, B -> x0
-          if (fxA != 1) pop[chk(row + xam, a.N)] = __float2half_rn(hA[k]);
-          pop[chk(row + x0, a.N)] = __float2half_rn(hB[k]);
+          if (fxA != 1) pop[chk(row + xam, a.N)] = __float2half_rn(h[k].x);
+          pop[chk(row + x0, a.N)] = __float2half_rn(h[k].y);
         }
       }
     }
   });
+}
+
+// ---------------------------------------------------------------------------------
+// Row-staged binary16 sweep: the plain A/B step of a binary16 lattice whose rows are
+// whole 16-byte multiples (nx % 8 == 0) and at least ROWS_MIN_NX long. A CTA walks
+// destination rows (y, z). One producer warp issues, per row, the 19 bulk copies
+// (cp.async.bulk, global -> shared, completing on the stage's "full" mbarrier) of the
+// source rows the pull reads -- population k of row (y - c_ky, z - c_kz) -- into a ring
+// of ROWS_STAGES shared-memory stages; eight consumer warps wait on a stage, compute
+// its row and release the stage on its "empty" mbarrier, so the two sides run
+// decoupled, without block-wide barriers. The x shift of the pull is an index into the
+// staged row. Whole rows in flight in shared memory replace loads held in registers,
+// which bounded the register-staged paired sweep (64 registers, 32 warps per SM,
+// latency-bound). Consumers compute node pairs (x0, x0 + 1) with the paired sweep's
+// per-node code (same closure, packed moments and collision), so the bits are those
+// of the single-node sweep; results go to global memory as half2 stores.
+// Every wait is bounded (STAGE_WAIT_LIMIT_NS); a warp that gives up sets
+// ERR_STAGE_WAIT in the lattice's error word and leaves, and the producer, before it
+// leaves, waits (bounded again) for the copies it has in flight.
+// ---------------------------------------------------------------------------------
+constexpr uint32_t ROWS_MIN_NX = 256;
+// nodes a stage holds at least (R = ceil(ROWS_STAGE_NODES / nx) rows)
+constexpr uint32_t ROWS_STAGE_NODES = 512;
+constexpr int ROWS_CONSUMER_WARPS = 8;
+constexpr int ROWS_THREADS = 32 * (ROWS_CONSUMER_WARPS + 1);
+constexpr uint64_t STAGE_WAIT_LIMIT_NS = 1000000000ull;  // 1 s: far beyond any copy's latency
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// One potentially blocking test of the phase: the thread may be suspended until the
+// phase completes or about `hint_ns` have passed, so waiting warps do not spin on the
+// issue slots the computing warps need.
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity, uint32_t hint_ns = 1000000u) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase of `parity` to complete; false once `limit_ns` have passed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
+}
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from global
+// to shared memory, counted on the mbarrier `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Loads from shared memory through 32-bit shared-window addresses (ld.shared: the
+// compiler cannot lose the state space the way it can for a generic pointer), and
+// half2 stores through st.global.
+__device__ __forceinline__ float lds_half(uint32_t addr) {
+  unsigned short v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr) : "memory");
+  return __half2float(__ushort_as_half(v));
+}
+__device__ __forceinline__ void lds_half2(uint32_t addr, float& lo, float& hi) {
+  unsigned int v;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  lo = __half2float(__ushort_as_half(static_cast<unsigned short>(v & 0xffffu)));
+  hi = __half2float(__ushort_as_half(static_cast<unsigned short>(v >> 16)));
+}
+__device__ __forceinline__ void stg_half2(__half* p, float lo, float hi) {
+  const __half2 v = __floats2half2_rn(lo, hi);
+  asm volatile("st.global.b32 [%0], %1;" ::"l"(p), "r"(*reinterpret_cast<const unsigned int*>(&v)) : "memory");
+}
+
+template <int STAGES>
+__global__ void __launch_bounds__(ROWS_THREADS, 3) sweep_rows_kernel(const __grid_constant__ SweepArgs a) {
+  extern __shared__ __align__(128) unsigned char rows_smem[];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
+  const uint32_t nx = a.nx, nrows = a.ny * a.nz;
+  const bool px = a.periodic & 1u, py = a.periodic & 2u, pz = a.periodic & 4u;
+  const __half* stage0 = reinterpret_cast<const __half*>(rows_smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1u);
+      mbar_init(smem_u32(&empty[s]), uint32_t(ROWS_CONSUMER_WARPS));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  // a stage holds R consecutive rows, R * nx / 2 >= the consumer threads when nx allows
+  const uint32_t R = (ROWS_STAGE_NODES + nx - 1) / nx;
+  const uint32_t ngroups = (nrows + R - 1) / R;
+  if (warp == ROWS_CONSUMER_WARPS) {
+    // producer: one lane issues every copy of this CTA's row groups (measured faster
+    // than spreading the 19 populations over the warp's lanes: 1.77 against 1.85 ms per
+    // 512^3 step; issuing faster only sharpened the read bursts)
+    if (lane != 0) return;
+    const uint32_t row_bytes = nx * uint32_t(sizeof(__half));
+    uint32_t i = 0;
+    for (;; ++i) {
+      const uint32_t g = blockIdx.x + i * gridDim.x;
+      if (g >= ngroups) break;
+      const int s = int(i % STAGES);
+      if (i >= uint32_t(STAGES) &&
+          !mbar_wait_bounded(smem_u32(&empty[s]), ((i / STAGES) - 1u) & 1u, STAGE_WAIT_LIMIT_NS)) {
+        if (a.err) atomicOr(a.err, ERR_STAGE_WAIT);
+        break;
+      }
+      const uint32_t r0 = g * R;
+      const uint32_t rows_here = nrows - r0 < R ? nrows - r0 : R;
+      const uint32_t bar = smem_u32(&full[s]);
+      mbar_expect_tx(bar, Q * row_bytes * rows_here);
+      for (uint32_t j = 0; j < rows_here; ++j) {
+        const uint32_t r = r0 + j;
+        const uint32_t z = fdiv(a.div_ny, r);
+        const uint32_t y = r - z * a.ny;
+        const uint32_t ym = y ? y - 1 : (py ? a.ny - 1 : 0);
+        const uint32_t yp = (y + 1 < a.ny) ? y + 1 : (py ? 0 : a.ny - 1);
+        const uint32_t zm = z ? z - 1 : (pz ? a.nz - 1 : 0);
+        const uint32_t zp = (z + 1 < a.nz) ? z + 1 : (pz ? 0 : a.nz - 1);
+        static_for<0, Q>([&](auto kc) {
+          constexpr int k = decltype(kc)::value;
+          const uint32_t sy = cy(k) > 0 ? ym : (cy(k) < 0 ? yp : y);
+          const uint32_t sz = cz(k) > 0 ? zm : (cz(k) < 0 ? zp : z);
+          const uint32_t srow = chk(sz * a.ny + sy, nrows);
+          const __half* src = static_cast<const __half*>(a.src_pop[k]) + size_t(srow) * nx;
+          bulk_g2s(smem_u32(stage0 + ((size_t(s) * Q + k) * R + j) * nx), src, row_bytes, bar);
+        });
+      }
+    }
+    // the copies of the last (up to STAGES) groups issued may still be in flight: the
+    // consumers wait for them; if the loop ended early, wait for them here (bounded)
+    if (blockIdx.x + i * gridDim.x < ngroups) {
+      for (uint32_t j = (i > uint32_t(STAGES) ? i - STAGES : 0); j < i; ++j)
+        (void)mbar_wait_bounded(smem_u32(&full[j % STAGES]), (j / STAGES) & 1u, STAGE_WAIT_LIMIT_NS);
+    }
+    return;
+  }
+  // consumers: 256 threads over the node pairs of the group's rows
+  const uint32_t npairs = nx >> 1;
+  for (uint32_t i = 0;; ++i) {
+    const uint32_t g = blockIdx.x + i * gridDim.x;
+    if (g >= ngroups) break;
+    const int s = int(i % STAGES);
+    if (!mbar_wait_bounded(smem_u32(&full[s]), (i / STAGES) & 1u, STAGE_WAIT_LIMIT_NS)) {
+      if (a.err) atomicOr(a.err, ERR_STAGE_WAIT);
+      return;
+    }
+    const uint32_t r0 = g * R;
+    const uint32_t rows_here = nrows - r0 < R ? nrows - r0 : R;
+    uint32_t j = 0, p = threadIdx.x;  // row of the group and pair of the row
+    while (p >= npairs) {
+      p -= npairs;
+      ++j;
+    }
+    for (; j < rows_here; p += 32u * ROWS_CONSUMER_WARPS) {
+      while (p >= npairs) {
+        p -= npairs;
+        ++j;
+      }
+      if (j >= rows_here) break;
+      const uint32_t r = r0 + j;
+      // shared address of row j of population 0 in stage s
+      const uint32_t st = smem_u32(stage0) + uint32_t(((size_t(s) * Q * R + j) * nx) * sizeof(__half));
+      const uint32_t z = fdiv(a.div_ny, r);
+      const uint32_t y = r - z * a.ny;
+      const int fy = py ? 0 : (y == 0 ? 1 : (y == a.ny - 1 ? 2 : 0));
+      const int fz = pz ? 0 : (z == 0 ? 1 : (z == a.nz - 1 ? 2 : 0));
+      const uint32_t x0 = 2u * p;
+      const uint32_t xam = x0 ? x0 - 1 : (px ? nx - 1 : 0);
+      const uint32_t xbp = (x0 + 2 < nx) ? x0 + 2 : (px ? 0 : nx - 1);
+      f32x2 h[Q];
+      const uint32_t row_stride = R * nx * uint32_t(sizeof(__half));  // population k -> k + 1
+      static_for<0, Q>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        const uint32_t row = st + uint32_t(k) * row_stride;
+        if constexpr (cx(k) == 0) {
+          lds_half2(row + 2u * x0, h[k].x, h[k].y);
+        } else if constexpr (cx(k) > 0) {  // pulled from x - 1
+          h[k].x = lds_half(row + 2u * xam);
+          h[k].y = lds_half(row + 2u * x0);
+        } else {  // pulled from x + 1
+          h[k].x = lds_half(row + 2u * (x0 + 1));
+          h[k].y = lds_half(row + 2u * xbp);
+        }
+      });
+      const int fxA = px ? 0 : (x0 == 0 ? 1 : 0);
+      const int fxB = px ? 0 : (x0 + 1 == nx - 1 ? 2 : 0);
+      const int codeA = fxA + 3 * fy + 9 * fz;
+      const int codeB = fxB + 3 * fy + 9 * fz;
+      if (codeA != 0) close_lane<0>(codeA, a, x0, y, z, h);
+      if (codeB != 0) close_lane<1>(codeB, a, x0 + 1, y, z, h);
+      const Moments<f32x2> m = moments(h, f32x2(a.rho0f));
+      collide(h, m, f32x2(a.omegaf));
+      const uint32_t cell = r * nx + x0;
+      static_for<0, Q>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        stg_half2(static_cast<__half*>(a.dst_pop[k]) + chk(cell, a.N - 1), h[k].x, h[k].y);
+      });
+    }
+    __syncwarp();  // the warp is done with stage s
+    if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+  }
 }
 
 // One time step of every lattice of a batch. A persistent grid draws chunks of the
@@ -1127,9 +1428,42 @@ void launch_sweep_mode(const SweepArgs& a, bool resid, cudaStream_t s) {
   else sweep_kernel<S, false, MODE, GEOM><<<blocks, SWEEP_THREADS, 0, s>>>(a);
 }
 
+// Stages of the row-staged sweep's shared-memory ring.
+constexpr int ROWS_STAGES = 2;
+
+// The row-staged binary16 sweep over every row of the lattice: a persistent grid of
+// SMs x the CTAs that fit per SM with the ring's shared memory. Returns
+// cudaErrorNotSupported when the ring does not fit (the caller then takes the paired
+// sweep).
+template <typename S>
+cudaError_t launch_rows(const SweepArgs& a, cudaStream_t s) {
+  static_assert(std::is_same<S, __half>::value, "the row-staged sweep is for binary16 storage");
+  const uint32_t R = (ROWS_STAGE_NODES + a.nx - 1) / a.nx;  // rows per stage (as the kernel)
+  const size_t smem = size_t(ROWS_STAGES) * Q * R * a.nx * sizeof(__half);
+  const void* fn = reinterpret_cast<const void*>(sweep_rows_kernel<ROWS_STAGES>);
+  int dev = 0, sms = 0, per = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (smem + ROWS_STAGES * sizeof(uint64_t) > size_t(optin)) return cudaErrorNotSupported;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, ROWS_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  if (per < 1) return cudaErrorNotSupported;
+  const uint32_t ngroups = (a.ny * a.nz + R - 1) / R;
+  const uint32_t grid = uint32_t(sms * per) < ngroups ? uint32_t(sms * per) : ngroups;
+  sweep_rows_kernel<ROWS_STAGES><<<grid, ROWS_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename S>
 cudaError_t launch_sweep_impl(const SweepArgs& a, bool resid, int mode, cudaStream_t s) {
   if constexpr (std::is_same<S, __half>::value) {
+    if (!resid && !a.links && !a.forced && mode == STREAM_AB && a.nx % 8 == 0 && a.nx >= ROWS_MIN_NX) {
+      const cudaError_t e = launch_rows<S>(a, s);
+      if (e != cudaErrorNotSupported) return e;
+    }
     if (!resid && !a.links && !a.forced && (a.nx & 1u) == 0) {
       const uint32_t blocks = sweep_blocks(a.N >> 1);
       if (mode == STREAM_AA_GATHER) sweep_pair_kernel<S, STREAM_AA_GATHER><<<blocks, SWEEP_THREADS, 0, s>>>(a);

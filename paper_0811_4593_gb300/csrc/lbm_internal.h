@@ -72,7 +72,13 @@ struct SweepArgs {
   double force[3];        // F: momentum the collision adds per step
   double tforce[3];       // tau F: the equilibrium velocity shift times rho
   float forcef[3], tforcef[3];
+  // Device word a sweep sets (bit 0) when it gave up waiting for its staged loads (a
+  // bounded wait ran out); the host reads and clears it at its synchronisation points.
+  uint32_t* err;
 };
+
+// Error bits of SweepArgs::err.
+constexpr uint32_t ERR_STAGE_WAIT = 1u;
 
 // Geometry word of a node: bits 0..18 (nodes without a rule): the pull source of
 // population k is solid (mid-grid bounce-back); bits 24..29: the node's on-site rule

@@ -48,6 +48,7 @@ struct lbm_ctx {
   void* snap = nullptr;
   double* partials = nullptr;
   double* dred = nullptr;
+  uint32_t* derr = nullptr;  // device error word of the sweeps (SweepArgs::err)
   cudaStream_t stream = nullptr;
   int64_t steps = 0, launches = 0, device_bytes = 0;
   std::string err = "no error";
@@ -308,6 +309,20 @@ lbm_status settle(lbm_ctx* ctx) {
 }
 
 // Final fold of the partial sums and the host-side residual.
+// Reads (and clears) the sweeps' device error word after synchronising the stream: a
+// sweep that gave up waiting for its staged loads left results that are not valid.
+lbm_status check_device_error(lbm_ctx* ctx) {
+  LBM_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "stream synchronisation");
+  if (!ctx->derr) return LBM_OK;
+  uint32_t v = 0;
+  LBM_CUDA(ctx, cudaMemcpyAsync(&v, ctx->derr, sizeof v, cudaMemcpyDeviceToHost, ctx->stream), "reading the error word");
+  LBM_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "reading the error word");
+  if (v == 0) return LBM_OK;
+  LBM_CUDA(ctx, cudaMemsetAsync(ctx->derr, 0, sizeof v, ctx->stream), "clearing the error word");
+  return fail(ctx, LBM_ERR_CUDA,
+              "a sweep gave up waiting for its staged row copies (device error word 0x%x): the state is not valid", v);
+}
+
 lbm_status finish_reduction(lbm_ctx* ctx, double* residual, double* mass) {
   LBM_CUDA(ctx, lbm::launch_final_reduce(ctx->partials, lbm::sweep_blocks(ctx->N), ctx->dred, ctx->stream),
            "final reduction launch");
@@ -315,6 +330,7 @@ lbm_status finish_reduction(lbm_ctx* ctx, double* residual, double* mass) {
   double h[4];
   LBM_CUDA(ctx, cudaMemcpyAsync(h, ctx->dred, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "reading reductions");
   LBM_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "synchronising after reductions");
+  if (lbm_status st = check_device_error(ctx); st != LBM_OK) return st;
   const double r = h[2] > 0.0 ? std::sqrt(h[1]) / std::sqrt(h[2]) : std::sqrt(h[1]);
   if (residual) *residual = r;
   if (mass) *mass = h[0];
@@ -381,9 +397,14 @@ lbm_status lbm_create_scheme(int nx, int ny, int nz, double tau, const lbm_face_
   if (scheme == LBM_SCHEME_AA) ctx->buf[1] = ctx->buf[0];
   ctx->dred = static_cast<double*>(ctx_alloc(ctx, 4 * sizeof(double)));
   if (!ctx->dred) return bail(fail(ctx, LBM_ERR_OOM, "allocation of the reduction result failed"));
+  ctx->derr = static_cast<uint32_t*>(ctx_alloc(ctx, sizeof(uint32_t)));
+  if (!ctx->derr) return bail(fail(ctx, LBM_ERR_OOM, "allocation of the error word failed"));
+  e = cudaMemsetAsync(ctx->derr, 0, sizeof(uint32_t), ctx->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "clearing the error word"));
 
   lbm::SweepArgs& a = ctx->args;
   a.nx = nx; a.ny = ny; a.nz = nz; a.N = ctx->N;
+  a.err = ctx->derr;
   a.div_nx = lbm::make_fastdiv(uint32_t(nx));
   a.div_ny = lbm::make_fastdiv(uint32_t(ny));
   a.div_nxh = lbm::make_fastdiv(uint32_t(nx / 2 > 0 ? nx / 2 : 1));
@@ -561,7 +582,7 @@ static lbm_status copy_populations(lbm_ctx* ctx, void* host_or_dev, int z0, int 
     LBM_CUDA(ctx, cudaMemcpyAsync(to_ctx ? l : u, to_ctx ? u : l, slab, kind, ctx->stream), "population copy");
   }
   LBM_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "synchronising the population copy");
-  return LBM_OK;
+  return to_ctx ? LBM_OK : check_device_error(ctx);
 }
 
 lbm_status lbm_set_populations(lbm_ctx* ctx, const void* src, int z0, int nzs, lbm_memory where) {
@@ -765,7 +786,7 @@ lbm_status lbm_sync(lbm_ctx* ctx) {
   DeviceGuard g(ctx->device);
   LBM_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "stream synchronisation");
   LBM_CUDA(ctx, cudaGetLastError(), "pending error");
-  return LBM_OK;
+  return check_device_error(ctx);
 }
 
 lbm_status lbm_info(const lbm_ctx* ctx, lbm_info_t* out) {

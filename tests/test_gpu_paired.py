@@ -1,10 +1,11 @@
-"""GPU tests of the paired binary16 sweep (two neighbouring nodes per thread).
+"""GPU tests of the paired binary16 sweeps (two neighbouring nodes per thread).
 
-Plain A/B steps of a binary16 lattice with an even nx run the paired sweep; residual
-steps, odd nx, geometries and forces run the single-node sweep. Both apply the same
-per-node code, so a lattice advanced by plain steps must hold exactly the bits of the
-same lattice advanced by residual steps, and it must match the FP64 oracle within the
-binary16 bar.
+Plain A/B steps of a binary16 lattice with an even nx run a paired sweep: the
+row-staged one (whole rows copied to shared memory by bulk copies) when nx is a
+multiple of 8 and at least 256, else the register-staged one; residual steps, odd nx,
+geometries and forces run the single-node sweep. All apply the same per-node code, so a
+lattice advanced by plain steps must hold exactly the bits of the same lattice advanced
+by residual steps, and it must match the FP64 oracle within the binary16 bar.
 """
 import numpy as np
 import pytest
@@ -35,6 +36,11 @@ WORKLOADS = {
     "periodic": lambda: inp.make_workload("periodic", 10, 7, 5, 0.6, [None] * 6),
     "couette": lambda: inp.couette(),
     "smallest": lambda: inp.random_face_workload(29, 4, 3, 3, 1.0, (False, False, False)),
+    # rows of 256 or more nodes that are whole 16-byte multiples: the row-staged sweep
+    "rows_channel": lambda: inp.channel(256, 6, 5, 0.7, (0.04, 0.01, 0.0)),
+    "rows_duct": lambda: inp.duct(264, 9, 7, 0.8, 0.05, 30.0),
+    "rows_xper": lambda: inp.random_face_workload(31, 512, 4, 5, 1.2, (True, False, False)),
+    "rows_all_periodic": lambda: inp.make_workload("periodic", 256, 3, 4, 0.6, [None] * 6),
 }
 
 
@@ -55,7 +61,7 @@ def test_paired_sweep_equals_single_node_sweep(name):
         np.testing.assert_array_equal(a.get_populations(), b.get_populations())
 
 
-@pytest.mark.parametrize("name", ["channel", "pressure", "periodic"])
+@pytest.mark.parametrize("name", ["channel", "pressure", "periodic", "rows_channel", "rows_xper"])
 def test_paired_sweep_matches_oracle(name):
     wl = WORKLOADS[name]()
     f0 = noisy_state((19, wl.nz, wl.ny, wl.nx), 9, u=(0.01, -0.004, 0.006))
