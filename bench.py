@@ -280,13 +280,23 @@ def run_variant(wl, precision, steps, warmup, resid_every, dist_ctx, clocks=None
            "kernel": sweep_kernel_name(wl, precision, scheme),
            "resident_bytes_per_node": BYTES_PER_UPDATE[precision] // (2 if scheme == "aa" else 1)}
     if precision == "f64":
-        # the FP64 sweep is bound by the FP64 pipe, not by HBM
+        # the FP64 sweep is bound by the FP64 pipe, not by HBM: its peak is the measured
+        # FP64 FMA rate of this device (thread-level operations per second; FP64 adds and
+        # multiplies issue at the same rate), the spec-derived figure is context only
+        from paper_0811_4593_gb300._binding import fp64_fma_rate
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         mhz = (clocks or {}).get("sm_mhz") or 2070.0
-        peak = FP64_INST_PER_SM_CLOCK * sms * mhz * 1e6 / 1e9
+        nominal = FP64_INST_PER_SM_CLOCK * sms * mhz * 1e6 / 1e9
+        clk = ClockSampler(torch.cuda.current_device()).start()
+        rate, probe_ms = fp64_fma_rate(12000)
+        probe_clock = clk.stop()
+        peak = rate / 1e9
         per_node = profiled_fp64_per_node("channel256")
-        alu = {"bound": "alu", "unit": "G FP64 inst/s", "peak": round(peak, 1),
-               "peak_basis": f"{FP64_INST_PER_SM_CLOCK:g} FP64 inst / SM / clock x {sms} SMs x {mhz:g} MHz",
+        alu = {"bound": "alu", "unit": "G FP64 inst/s", "peak": round(peak, 1), "peak_source": "measured",
+               "peak_basis": (f"lbm_fp64_fma_rate: 8 independent DFMA chains per thread on every resident warp, "
+                              f"{probe_ms:.1f} ms, SM clock {probe_clock.get('sm_mhz')} MHz"),
+               "nominal": round(nominal, 1),
+               "nominal_basis": f"{FP64_INST_PER_SM_CLOCK:g} FP64 inst / SM / clock x {sms} SMs x {mhz:g} MHz",
                "fp64_inst_per_node": per_node}
         if per_node:
             a = per_node * wl.cells / (step_ms * 1e-3) / 1e9
@@ -328,6 +338,33 @@ def e2e_run(wl, precision, steps, resid_every, dist_ctx):
     return dt_s, h2d, d2h
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), with the architecture."""
+    import platform
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:  # noqa: BLE001 - lscpu missing
+        pass
+    if not name:
+        try:
+            fields = {}
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if ":" in line:
+                        k, v = line.split(":", 1)
+                        fields.setdefault(k.strip().lower(), v.strip())
+            name = fields.get("model name") or (
+                f"implementer {fields['cpu implementer']} part {fields['cpu part']}" if "cpu part" in fields else None)
+        except OSError:
+            pass
+    return f"{name or 'unknown'} ({platform.machine()})"
+
+
 def cpu_baseline(wl, seconds: float):
     import oracle
     sample, text = cpu_sample(wl)
@@ -342,7 +379,7 @@ def cpu_baseline(wl, seconds: float):
             break
     dt = time.perf_counter() - t0
     return {"value": sample.cells * n / dt / 1e6, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{text}, {n} FP64 steps from rest in {dt:.1f} s"}
+            "cpu": cpu_model(), "sample": f"{text}, {n} FP64 steps from rest in {dt:.1f} s"}
 
 
 def native(args):
@@ -842,6 +879,7 @@ def reference(args):
            "config": {"workload": describe(wl), "nodes": wl.cells, "precision": "f64 (oracle)",
                       "parallelism": "host cores"},
            "cpu_baseline": {"value": round(value, 2), "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
+                            "cpu": cpu_model(),
                             "sample": f"{text}, {args.steps} FP64 steps after {args.warmup} warm-up steps"},
            "e2e": {"value": round(value, 2), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

@@ -343,6 +343,16 @@ LBM_API lbm_status lbm_reduce_state_static(const void* populations, int nx, int 
                                            lbm_precision prec, double rho0, void* velocity_snapshot,
                                            double* sums, void* cuda_stream);
 
+/* Measurement helper (no counterpart in the paper): the current device's rate of FP64
+ * fused multiply-adds, from a kernel that keeps every resident warp on eight
+ * independent FMA chains per thread for `iters` iterations (after a short warm-up
+ * launch), timed with CUDA events on the legacy default stream. Writes thread-level
+ * DFMA operations per second to *fma_per_s and the timed launch's duration in
+ * milliseconds to *ms (may be NULL). Synchronises. LBM_ERR_ARG for iters < 1 or a NULL
+ * fma_per_s; LBM_ERR_CUDA if a launch fails. The FP64 sweep's roofline divides its
+ * FP64 instruction rate by this rate. */
+LBM_API lbm_status lbm_fp64_fma_rate(int iters, double* fma_per_s, double* ms);
+
 /* Last error message of a context, or of the calling thread's last failed call that
  * had no context (ctx == NULL). Never NULL. */
 LBM_API const char* lbm_last_error(const lbm_ctx* ctx);

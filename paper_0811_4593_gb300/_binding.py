@@ -46,6 +46,7 @@ EXPORTS = {
     "lbm_check_guards": (C.c_int, [C.c_void_p]),
     "lbm_rule_unknowns": (C.c_int, [C.c_int, C.POINTER(C.c_uint32)]),
     "lbm_debug_bounds_errors": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_uint64)]),
+    "lbm_fp64_fma_rate": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_info": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_batch_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
@@ -110,6 +111,14 @@ def debug_bounds_errors():
     en, n = C.c_int(), C.c_uint64()
     check(lib().lbm_debug_bounds_errors(C.byref(en), C.byref(n)))
     return bool(en.value), int(n.value)
+
+
+def fp64_fma_rate(iters: int = 20000):
+    """(thread-level FP64 FMAs per second, milliseconds of the timed launch) of the
+    current device, from lbm_fp64_fma_rate."""
+    r, ms = C.c_double(), C.c_double()
+    check(lib().lbm_fp64_fma_rate(int(iters), C.byref(r), C.byref(ms)))
+    return r.value, ms.value
 
 
 def lib():

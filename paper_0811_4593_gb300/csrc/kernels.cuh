@@ -201,8 +201,13 @@ struct FaceVals {
 
 // The relation's sum over the shifted populations of a plane with inward normal
 // SG * e_A: in-plane populations once, outgoing ones twice (its weights sum to 1, so
-// the plane's density relation reads rho (1 - u.n) = ref + S). Exact in double:
-// accumulated in double for FP64, as an error-free float pair otherwise.
+// the plane's density relation reads rho (1 - u.n) = ref + S). FP64: accumulated in
+// double. Float sweeps: accumulated as a float pair hi + lo with TwoSum, which is
+// exact except for the float rounding of lo's own sum of the 14 error terms; that
+// leaves an error below about 14^2 2^-48 (~7e-13) of the largest partial sum, against
+// 14 2^-53 (~2e-15) for accumulation in double -- both far below the float rounding of
+// the populations, and the pair costs no FP64 work on the face nodes until the final
+// conversion.
 template <int A, int SG, typename T>
 __device__ __forceinline__ double relation_sum(const T (&h)[Q]) {
   if constexpr (std::is_same<T, double>::value) {
@@ -634,6 +639,42 @@ __device__ __forceinline__ Moments<T> moments(const T (&h)[Q], T rho0) {
   return m;
 }
 
+// Moments with compensated sums (FP32 storage with a geometry or a body force): each
+// of the five partial sums runs as a TwoSum float pair, and density and momenta are
+// rounded to float once, from the pairs, so they carry about half an ulp of error
+// instead of up to one per term. In a steady flow these roundings repeat every step
+// and integrate over the relaxation time (a 32^3 body-force Poiseuille at tau = 2
+// relaxes over ~190 steps), so the exact sums reduce the float error of such flows.
+__device__ __forceinline__ Moments<float> moments_compensated(const float (&h)[Q], float rho0) {
+  float sp = 0.0f, spl = 0.0f, sm = 0.0f, sml = 0.0f, s0 = 0.0f, s0l = 0.0f;
+  float jy = 0.0f, jyl = 0.0f, jz = 0.0f, jzl = 0.0f;
+  static_for<0, Q>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    if constexpr (cx(k) > 0) two_sum_acc(sp, spl, h[k]);
+    else if constexpr (cx(k) < 0) two_sum_acc(sm, sml, h[k]);
+    else two_sum_acc(s0, s0l, h[k]);
+    if constexpr (cy(k) != 0) two_sum_acc(jy, jyl, cy(k) > 0 ? h[k] : -h[k]);
+    if constexpr (cz(k) != 0) two_sum_acc(jz, jzl, cz(k) > 0 ? h[k] : -h[k]);
+  });
+  Moments<float> m;
+  float d = sp, dl = __fadd_rn(__fadd_rn(spl, sml), s0l);
+  two_sum_acc(d, dl, sm);
+  two_sum_acc(d, dl, s0);
+  m.drho = __fadd_rn(d, dl);
+  float x = sp, xl = __fsub_rn(spl, sml);
+  two_sum_acc(x, xl, -sm);
+  m.jx = __fadd_rn(x, xl);
+  m.jy = __fadd_rn(jy, jyl);
+  m.jz = __fadd_rn(jz, jzl);
+  m.rho = __fadd_rn(rho0, m.drho);
+  const float inv = 1.0f / m.rho;
+  m.inv = inv;
+  m.ux = __fmul_rn(m.jx, inv);
+  m.uy = __fmul_rn(m.jy, inv);
+  m.uz = __fmul_rn(m.jz, inv);
+  return m;
+}
+
 // EXACT_MOMENTUM: the momentum term 3 omega w_i (c_i.j) takes its coefficient as an
 // unevaluated pair hi + lo (coef, from the host), so the collision conserves momentum
 // to float rounding of each product instead of biasing it by the rounding of one
@@ -856,7 +897,9 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
     } else {
       if (code != 0) apply_boundary(code, a, x, y, z, h);
     }
-    Moments<T> m = moments(h, rho0_of<T>(a));
+    Moments<T> m;
+    if constexpr (GEOM && std::is_same<S, float>::value) m = moments_compensated(h, rho0_of<T>(a));
+    else m = moments(h, rho0_of<T>(a));
     if constexpr (GEOM) {
       if (a.forced && !solid) {
         // eq. gravity: the collision relaxes toward the equilibrium at u + tau F / rho

@@ -104,7 +104,15 @@ def test_corner_codes_equal_box_corners_bitwise(prec):
         np.testing.assert_array_equal(b.get_populations()[:, 1:-1, 1:-1, 1:-1], a.get_populations())
 
 
-@pytest.mark.parametrize("prec,tau,steps", [("f64", 2.0, 7000), ("f64", 1.0, 20000), ("f32", 2.0, 7000)])
+# FP32 bars: the benchmark spec's 1e-5 at the paper's tau = 2 (measured 9.1e-6 with the
+# compensated moment sums of the geometry/force sweep); at tau = 1 float storage alone
+# (FP64 arithmetic on a state rounded to shifted float every step) leaves 1.1e-5 in this
+# steady flow, and the float sweep measures 2.0e-5, so its bar is 2.5e-5
+BODY_FORCE_TOL = {("f64", 2.0): 1e-9, ("f64", 1.0): 1e-9, ("f32", 2.0): 1e-5, ("f32", 1.0): 2.5e-5}
+
+
+@pytest.mark.parametrize("prec,tau,steps", [("f64", 2.0, 7000), ("f64", 1.0, 20000), ("f32", 2.0, 7000),
+                                            ("f32", 1.0, 20000)])
 def test_body_force_poiseuille_32_cubed(prec, tau, steps):
     # the paper's body-force check: 32^3, walls on the x faces, periodic y and z; the
     # velocity after the boundary rule is the parabola of eq. poiseuille with the
@@ -121,7 +129,7 @@ def test_body_force_poiseuille_32_cubed(prec, tau, steps):
     h = (wl.nx - 1) / 2.0
     exact = F / (2.0 * rho * (tau - 0.5) / 3.0) * (h * h - (x - h) ** 2)
     err = np.abs(u_pre - exact).max() / exact.max()
-    assert err < (1e-9 if prec == "f64" else 1e-4), err
+    assert err < BODY_FORCE_TOL[(prec, tau)], err
     assert np.abs(u_pre[:, :, [0, -1]]).max() < (1e-15 if prec == "f64" else 1e-7)
 
 
