@@ -260,8 +260,8 @@ def sweep_kernel_name(wl, precision, scheme="ab"):
     """The kernel that runs the plain (non-residual) steps of a lattice."""
     if precision == "f16" and wl.nx % 2 == 0 and getattr(wl, "solid", None) is None \
             and getattr(wl, "force", None) is None:
-        if scheme == "ab" and wl.nx % 8 == 0 and wl.nx >= 256:
-            return "sweep_rows_kernel<f16>"
+        if wl.nx % 8 == 0 and wl.nx >= 256:
+            return "sweep_rows_kernel<f16>" + ("" if scheme == "ab" else " (AA steps)")
         return "sweep_pair_kernel<f16>" + ("" if scheme == "ab" else " (AA steps)")
     return f"sweep_kernel<{precision}>"
 

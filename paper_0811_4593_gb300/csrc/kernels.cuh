@@ -1209,7 +1209,13 @@ __device__ __forceinline__ void stg_half2(__half* p, float lo, float hi) {
   asm volatile("st.global.b32 [%0], %1;" ::"l"(p), "r"(*reinterpret_cast<const unsigned int*>(&v)) : "memory");
 }
 
-template <int STAGES>
+// MODE: STREAM_AB (pull from the other array, store in place), or the AA steps of an
+// even-nx binary16 lattice as in the single-node sweep: STREAM_AA_GATHER stages slot -k
+// of the pull sources and pushes f*_k to slot k of node x + c_k, STREAM_AA_LOCAL
+// stages the row's own slots and writes slot -k of the same node. In both AA steps
+// every node reads and writes only locations it alone owns, so staging a row before
+// other rows' nodes write theirs changes nothing.
+template <int STAGES, int MODE>
 __global__ void __launch_bounds__(ROWS_THREADS, 3) sweep_rows_kernel(const __grid_constant__ SweepArgs a) {
   extern __shared__ __align__(128) unsigned char rows_smem[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
@@ -1260,10 +1266,12 @@ __global__ void __launch_bounds__(ROWS_THREADS, 3) sweep_rows_kernel(const __gri
         const uint32_t zp = (z + 1 < a.nz) ? z + 1 : (pz ? 0 : a.nz - 1);
         static_for<0, Q>([&](auto kc) {
           constexpr int k = decltype(kc)::value;
-          const uint32_t sy = cy(k) > 0 ? ym : (cy(k) < 0 ? yp : y);
-          const uint32_t sz = cz(k) > 0 ? zm : (cz(k) < 0 ? zp : z);
+          constexpr bool local = MODE == STREAM_AA_LOCAL;
+          const uint32_t sy = (local || cy(k) == 0) ? y : (cy(k) > 0 ? ym : yp);
+          const uint32_t sz = (local || cz(k) == 0) ? z : (cz(k) > 0 ? zm : zp);
           const uint32_t srow = chk(sz * a.ny + sy, nrows);
-          const __half* src = static_cast<const __half*>(a.src_pop[k]) + size_t(srow) * nx;
+          constexpr int slot = MODE == STREAM_AA_GATHER ? opp(k) : k;
+          const __half* src = static_cast<const __half*>(a.src_pop[slot]) + size_t(srow) * nx;
           bulk_g2s(smem_u32(stage0 + ((size_t(s) * Q + k) * R + j) * nx), src, row_bytes, bar);
         });
       }
@@ -1314,7 +1322,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 3) sweep_rows_kernel(const __gri
       static_for<0, Q>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
         const uint32_t row = st + uint32_t(k) * row_stride;
-        if constexpr (cx(k) == 0) {
+        if constexpr (cx(k) == 0 || MODE == STREAM_AA_LOCAL) {
           lds_half2(row + 2u * x0, h[k].x, h[k].y);
         } else if constexpr (cx(k) > 0) {  // pulled from x - 1
           h[k].x = lds_half(row + 2u * xam);
@@ -1333,10 +1341,39 @@ __global__ void __launch_bounds__(ROWS_THREADS, 3) sweep_rows_kernel(const __gri
       const Moments<f32x2> m = moments(h, f32x2(a.rho0f));
       collide(h, m, f32x2(a.omegaf));
       const uint32_t cell = r * nx + x0;
-      static_for<0, Q>([&](auto kc) {
-        constexpr int k = decltype(kc)::value;
-        stg_half2(static_cast<__half*>(a.dst_pop[k]) + chk(cell, a.N - 1), h[k].x, h[k].y);
-      });
+      if constexpr (MODE == STREAM_AA_GATHER) {
+        // push f*_k to slot k of node x + c_k; a target beyond a walled face does not exist
+        const uint32_t ym = y ? y - 1 : (py ? a.ny - 1 : 0);
+        const uint32_t yp = (y + 1 < a.ny) ? y + 1 : (py ? 0 : a.ny - 1);
+        const uint32_t zm = z ? z - 1 : (pz ? a.nz - 1 : 0);
+        const uint32_t zp = (z + 1 < a.nz) ? z + 1 : (pz ? 0 : a.nz - 1);
+        static_for<0, Q>([&](auto kc) {
+          constexpr int k = decltype(kc)::value;
+          const bool in_yz = !((fy == 1 && cy(k) < 0) || (fy == 2 && cy(k) > 0) || (fz == 1 && cz(k) < 0) ||
+                               (fz == 2 && cz(k) > 0));
+          if (in_yz) {
+            __half* pop = static_cast<__half*>(a.dst_pop[k]);
+            const uint32_t ty = cy(k) > 0 ? yp : (cy(k) < 0 ? ym : y);
+            const uint32_t tz = cz(k) > 0 ? zp : (cz(k) < 0 ? zm : z);
+            const uint32_t trow = (tz * a.ny + ty) * nx;
+            if constexpr (cx(k) == 0) {
+              stg_half2(pop + chk(trow + x0, a.N - 1), h[k].x, h[k].y);
+            } else if constexpr (cx(k) > 0) {  // A -> x0 + 1, B -> x0 + 2
+              pop[chk(trow + x0 + 1, a.N)] = __float2half_rn(h[k].x);
+              if (fxB != 2) pop[chk(trow + xbp, a.N)] = __float2half_rn(h[k].y);
+            } else {  // A -> x0 - 1, B -> x0
+              if (fxA != 1) pop[chk(trow + xam, a.N)] = __float2half_rn(h[k].x);
+              pop[chk(trow + x0, a.N)] = __float2half_rn(h[k].y);
+            }
+          }
+        });
+      } else {
+        static_for<0, Q>([&](auto kc) {
+          constexpr int k = decltype(kc)::value;
+          constexpr int slot = MODE == STREAM_AA_LOCAL ? opp(k) : k;
+          stg_half2(static_cast<__half*>(a.dst_pop[slot]) + chk(cell, a.N - 1), h[k].x, h[k].y);
+        });
+      }
     }
     __syncwarp();  // the warp is done with stage s
     if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
@@ -1478,12 +1515,12 @@ constexpr int ROWS_STAGES = 2;
 // SMs x the CTAs that fit per SM with the ring's shared memory. Returns
 // cudaErrorNotSupported when the ring does not fit (the caller then takes the paired
 // sweep).
-template <typename S>
+template <typename S, int MODE>
 cudaError_t launch_rows(const SweepArgs& a, cudaStream_t s) {
   static_assert(std::is_same<S, __half>::value, "the row-staged sweep is for binary16 storage");
   const uint32_t R = (ROWS_STAGE_NODES + a.nx - 1) / a.nx;  // rows per stage (as the kernel)
   const size_t smem = size_t(ROWS_STAGES) * Q * R * a.nx * sizeof(__half);
-  const void* fn = reinterpret_cast<const void*>(sweep_rows_kernel<ROWS_STAGES>);
+  const void* fn = reinterpret_cast<const void*>(sweep_rows_kernel<ROWS_STAGES, MODE>);
   int dev = 0, sms = 0, per = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1496,15 +1533,17 @@ cudaError_t launch_rows(const SweepArgs& a, cudaStream_t s) {
   if (per < 1) return cudaErrorNotSupported;
   const uint32_t ngroups = (a.ny * a.nz + R - 1) / R;
   const uint32_t grid = uint32_t(sms * per) < ngroups ? uint32_t(sms * per) : ngroups;
-  sweep_rows_kernel<ROWS_STAGES><<<grid, ROWS_THREADS, smem, s>>>(a);
+  sweep_rows_kernel<ROWS_STAGES, MODE><<<grid, ROWS_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t launch_sweep_impl(const SweepArgs& a, bool resid, int mode, cudaStream_t s) {
   if constexpr (std::is_same<S, __half>::value) {
-    if (!resid && !a.links && !a.forced && mode == STREAM_AB && a.nx % 8 == 0 && a.nx >= ROWS_MIN_NX) {
-      const cudaError_t e = launch_rows<S>(a, s);
+    if (!resid && !a.links && !a.forced && a.nx % 8 == 0 && a.nx >= ROWS_MIN_NX) {
+      const cudaError_t e = mode == STREAM_AA_GATHER ? launch_rows<S, STREAM_AA_GATHER>(a, s)
+                            : mode == STREAM_AA_LOCAL ? launch_rows<S, STREAM_AA_LOCAL>(a, s)
+                                                      : launch_rows<S, STREAM_AB>(a, s);
       if (e != cudaErrorNotSupported) return e;
     }
     if (!resid && !a.links && !a.forced && (a.nx & 1u) == 0) {
