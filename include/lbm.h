@@ -233,6 +233,18 @@ LBM_API lbm_status lbm_check_guards(lbm_ctx* ctx);
  * (otherwise *count is 0). Synchronises the device. */
 LBM_API lbm_status lbm_debug_bounds_errors(int* enabled, uint64_t* count);
 
+/* Failure injection for tests (no counterpart in the paper). The binary16 sweep that
+ * stages rows in shared memory waits on its bulk copies with a time limit (about one
+ * second); when a wait runs out, the sweep sets the context's device error word and
+ * ends, and the next synchronising call (lbm_sync, lbm_step_residual, lbm_residual,
+ * lbm_get_populations) returns LBM_ERR_CUDA with a message that says so; the state
+ * of the steps since the previous such call is then not valid, but the context stays
+ * usable (load a state with lbm_set_populations). With enable != 0, later row-staged
+ * sweeps of `ctx` leave the copies of one row group un-issued, so that a wait runs
+ * out on purpose (no fault: the sweep ends after about two seconds); enable = 0 turns
+ * this off. Other sweep kernels ignore it. */
+LBM_API lbm_status lbm_debug_drop_staged_copies(lbm_ctx* ctx, int enable);
+
 /* Block the host until the context's stream is idle; reports asynchronous errors. */
 LBM_API lbm_status lbm_sync(lbm_ctx* ctx);
 

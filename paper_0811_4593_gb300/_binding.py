@@ -47,6 +47,7 @@ EXPORTS = {
     "lbm_rule_unknowns": (C.c_int, [C.c_int, C.POINTER(C.c_uint32)]),
     "lbm_debug_bounds_errors": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_uint64)]),
     "lbm_fp64_fma_rate": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "lbm_debug_drop_staged_copies": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_info": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_batch_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_void_p)]),

@@ -1256,6 +1256,7 @@ __global__ void __launch_bounds__(ROWS_THREADS, 3) sweep_rows_kernel(const __gri
       const uint32_t rows_here = nrows - r0 < R ? nrows - r0 : R;
       const uint32_t bar = smem_u32(&full[s]);
       mbar_expect_tx(bar, Q * row_bytes * rows_here);
+      if (a.drop_copies && blockIdx.x == 0 && i == 0) continue;  // test hook: the wait runs out
       for (uint32_t j = 0; j < rows_here; ++j) {
         const uint32_t r = r0 + j;
         const uint32_t z = fdiv(a.div_ny, r);

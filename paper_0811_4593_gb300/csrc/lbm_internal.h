@@ -75,6 +75,10 @@ struct SweepArgs {
   // Device word a sweep sets (bit 0) when it gave up waiting for its staged loads (a
   // bounded wait ran out); the host reads and clears it at its synchronisation points.
   uint32_t* err;
+  // Failure injection for tests of the bounded waits: nonzero makes the row-staged
+  // sweep's first CTA announce the copies of its first row group but not issue them,
+  // so its waits run out (no fault, no unbounded wait).
+  uint32_t drop_copies;
 };
 
 // Error bits of SweepArgs::err.

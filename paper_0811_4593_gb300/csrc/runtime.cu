@@ -781,6 +781,12 @@ lbm_status lbm_debug_bounds_errors(int* enabled, uint64_t* count) {
   return LBM_OK;
 }
 
+lbm_status lbm_debug_drop_staged_copies(lbm_ctx* ctx, int enable) {
+  if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+  ctx->args.drop_copies = enable ? 1u : 0u;
+  return LBM_OK;
+}
+
 lbm_status lbm_sync(lbm_ctx* ctx) {
   if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
   DeviceGuard g(ctx->device);
