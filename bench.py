@@ -819,6 +819,13 @@ def study_force(args):
           flush=True)
 
 
+def study_batched(args):
+    """The batched sweep alone on its fixed serving mix (the first 40 requests of the
+    seed-1 stream, all resident): launch time, MLUPS and HBM-roofline fraction."""
+    _gpu_study_setup()
+    print(json.dumps({"study": "batched sweep on a serving mix", **batched_sweep_roofline(args.precision)}), flush=True)
+
+
 def study_configs(args):
     """Throughput of the small configurations (Couette 8x8x17, 5000 steps; plane
     Poiseuille 4x4x256, tau 1, 15100 steps) on the GPU in each storage type and in the
@@ -900,7 +907,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true", help="run the serving mix instead of the sweep benchmark")
-    ap.add_argument("--study", choices=["tilted", "duct", "poiseuille", "duct-config", "force", "configs"],
+    ap.add_argument("--study", choices=["tilted", "duct", "poiseuille", "duct-config", "force", "configs", "batched"],
                     help="run a reproduction study instead of the benchmark")
     ap.add_argument("--study-steps", type=int, default=0, help="steps of the duct-config study (default 20000)")
     ap.add_argument("--requests", type=int, default=2000)
@@ -931,6 +938,8 @@ def main():
         study_force(args)
     elif args.study == "configs":
         study_configs(args)
+    elif args.study == "batched":
+        study_batched(args)
     elif args.serving:
         serving(args)
     else:
