@@ -482,6 +482,7 @@ def batched_sweep_roofline(precision: str, nlat: int = 40, steps: int = 100, war
             "grid": grid, "launch_ms": round(ms, 4), "mlups": round(nodes / (ms * 1e-3) / 1e6, 1), "bound": "hbm",
             "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
             "peak_source": src, "bytes_per_update": BYTES_PER_UPDATE[precision],
+            "traffic": profiled_traffic("batched", precision, f"serving{nlat}"),
             "mix": f"first {nlat} requests of the seed-1 serving stream, all resident"}
 
 
