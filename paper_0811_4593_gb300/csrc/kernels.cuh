@@ -173,6 +173,16 @@ template <> struct Storage<__half> {
   __device__ static __half store(float v) { return __float2half_rn(v); }
 };
 
+// Population load of a sweep step: the A/B step reads through the storage codec (for
+// FP32 with the L2 prefetch hint); the AA steps read plain read-only loads (with the
+// hint the FP32 AA steps, which write the array they read, measured 2.6 % slower).
+template <typename S, int MODE>
+__device__ __forceinline__ typename std::conditional<std::is_same<S, double>::value, double, float>::type
+load_pop(const S* p) {
+  if constexpr (MODE != 0 && std::is_same<S, float>::value) return __ldg(p);
+  else return Storage<S>::load(p);
+}
+
 // The reference density the register values are shifted by: rho0, or 0 for FP64.
 template <typename S>
 __device__ __forceinline__ double ref_rho(double rho0) { return Storage<S>::shifted ? rho0 : 0.0; }
@@ -866,9 +876,9 @@ __device__ __forceinline__ void sweep_block(const SweepArgs& a, uint32_t blk) {
         if constexpr (MODE == STREAM_AB) {
           h[k] = Storage<S>::load(static_cast<const S*>(a.src_pop[k]) + pull_idx(kc));
         } else if constexpr (MODE == STREAM_AA_GATHER) {
-          h[k] = Storage<S>::load(static_cast<const S*>(a.src_pop[opp(k)]) + pull_idx(kc));
+          h[k] = load_pop<S, MODE>(static_cast<const S*>(a.src_pop[opp(k)]) + pull_idx(kc));
         } else {
-          h[k] = Storage<S>::load(static_cast<const S*>(a.src_pop[k]) + cell);
+          h[k] = load_pop<S, MODE>(static_cast<const S*>(a.src_pop[k]) + cell);
         }
       });
     } else {
