@@ -41,6 +41,10 @@ WORKLOADS = {
     "rows_duct": lambda: inp.duct(264, 9, 7, 0.8, 0.05, 30.0),
     "rows_xper": lambda: inp.random_face_workload(31, 512, 4, 5, 1.2, (True, False, False)),
     "rows_all_periodic": lambda: inp.make_workload("periodic", 256, 3, 4, 0.6, [None] * 6),
+    # pressure planes at x = 0 and x = nx - 1, random velocity tables on every other face
+    # (faces, edges and corners of both kinds inside the staged rows)
+    "rows_pressure": lambda: inp.random_pressure_workload(32, 272, 5, 4, 0.9),
+    "rows_random_faces": lambda: inp.random_face_workload(33, 264, 4, 5, 1.1, (False, False, False)),
 }
 
 
@@ -61,12 +65,18 @@ def test_paired_sweep_equals_single_node_sweep(name):
         np.testing.assert_array_equal(a.get_populations(), b.get_populations())
 
 
-@pytest.mark.parametrize("name", ["channel", "pressure", "periodic", "rows_channel", "rows_xper"])
+# binary16 bars at about twice the measured velocity error (GB300: 3.9e-4, 2.4e-4, 3.9e-4,
+# 3.3e-4, 4.9e-4, 3.1e-4, 3.5e-4)
+PAIRED_F16_TOL = {"channel": 8e-4, "pressure": 5e-4, "periodic": 8e-4, "rows_channel": 7e-4, "rows_xper": 1e-3,
+                  "rows_pressure": 7e-4, "rows_random_faces": 7e-4}
+
+
+@pytest.mark.parametrize("name", list(PAIRED_F16_TOL))
 def test_paired_sweep_matches_oracle(name):
     wl = WORKLOADS[name]()
     f0 = noisy_state((19, wl.nz, wl.ny, wl.nx), 9, u=(0.01, -0.004, 0.006))
     got, ref = run_pair(wl, "f16", f0, 30)
-    assert velocity_error(wl, got, ref) <= 5e-3
+    assert velocity_error(wl, got, ref) <= PAIRED_F16_TOL[name]
     assert np.isfinite(decode(encode(got, "f16"), "f16")).all()
 
 
