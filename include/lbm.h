@@ -102,7 +102,11 @@ typedef struct {
 /* Device allocator hook: every device buffer the library owns is obtained through
  * alloc(bytes, user) and returned through release(ptr, user). Default: cudaMalloc and
  * cudaFree. Takes effect for allocations made after the call; release is always
- * called with the hook that allocated the pointer. NULL alloc restores the default. */
+ * called with the hook that allocated the pointer. NULL alloc restores the default.
+ * alloc must return memory aligned to 256 bytes (as cudaMalloc and PyTorch's caching
+ * allocator do): the sweeps read population rows with 16-byte bulk copies and 4-byte
+ * pair loads; a pointer with less alignment is returned through release at once and
+ * the allocation fails with LBM_ERR_OOM. */
 typedef void* (*lbm_alloc_fn)(size_t bytes, void* user);
 typedef void (*lbm_free_fn)(void* ptr, void* user);
 LBM_API lbm_status lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void* user);

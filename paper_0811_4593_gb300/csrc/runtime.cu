@@ -148,6 +148,13 @@ void* ctx_alloc(lbm_ctx* ctx, size_t bytes) {
     p = nullptr;
   }
   if (!p) return nullptr;
+  if (reinterpret_cast<uintptr_t>(p) % 256 != 0) {
+    // the sweeps' 16-byte bulk copies and pair loads need aligned buffers
+    if (ctx->release) ctx->release(p, ctx->user);
+    else cudaFree(p);
+    fail(ctx, LBM_ERR_OOM, "the allocator hook returned %p, which is not 256-byte aligned", p);
+    return nullptr;
+  }
   char* base = static_cast<char*>(p);
   if (cudaMemset(base, GUARD_BYTE, GUARD) != cudaSuccess ||
       cudaMemset(base + GUARD + bytes, GUARD_BYTE, GUARD) != cudaSuccess) {
