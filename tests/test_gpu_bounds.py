@@ -53,6 +53,18 @@ with lbm.Batch(4, "f32") as b:
     for lat in lats:
         lat.close()
 ran.append(("batch", "f32", "ab"))
+for prec in ("f32", "f16"):
+    with lbm.Batch(4, prec) as b:                   # AA lattices: both batched AA steps
+        lats = [lbm.Lattice.from_workload(w, prec, scheme="aa") for w in
+                (inp.duct(37, 19, 23, 0.8, 0.05, 30.0), inp.channel(33, 20, 21, 0.7, (0.04, 0.01, 0.0)),
+                 inp.random_pressure_workload(28, 13, 10, 11, 0.9), inp.couette())]
+        for i, lat in enumerate(lats):
+            b.attach(i, lat)
+        b.step(10, residual=True)
+        b.step(4)
+        for lat in lats:
+            lat.close()
+    ran.append(("batch", prec, "aa"))
 enabled, count = debug_bounds_errors()
 print(json.dumps({"enabled": enabled, "count": count, "lattices": len(ran)}))
 """
