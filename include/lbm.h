@@ -142,7 +142,11 @@ LBM_API lbm_status lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
  * unknown populations eq. f5, eqs. f9-f17 with the corrections eqs. Nx, Ny (and their
  * appendix analogues for the other planes); on edge and corner nodes bounce-back with
  * the edge correction eq. edge, buried links eq. buried and eq. corner; then BGK
- * collision (eq. bgk, eq. feq). */
+ * collision (eq. bgk, eq. feq). Binary16 lattices whose rows are multiples of 8 nodes
+ * and at least 256 long take a sweep that stages population rows in shared memory with
+ * bulk copies; its waits are bounded, and one that runs out is reported by the next
+ * synchronising call as LBM_ERR_CUDA (see lbm_debug_drop_staged_copies). Every sweep
+ * variant computes the same bits for a node. */
 LBM_API lbm_status lbm_step(lbm_ctx* ctx, int n);
 
 /* Advance n >= 1 steps like lbm_step, the last one also forming, in double, the
