@@ -1225,6 +1225,36 @@ __device__ __forceinline__ void stg_half2(__half* p, float lo, float hi) {
 // stages the row's own slots and writes slot -k of the same node. In both AA steps
 // every node reads and writes only locations it alone owns, so staging a row before
 // other rows' nodes write theirs changes nothing.
+// Push of the AA gather step for the pair (x0, x0 + 1) of the row-staged sweep: f*_k of
+// each node to slot k of node x + c_k, whose row starts zoff[1 + c_z] + yoff[1 + c_y] - x0
+// cells into the array (yoff carries x0). CHECK: the pair lies on a walled y or z face
+// (fy, fz != 0), where a target beyond the face does not exist; a target beyond a
+// walled x face (node A of the first pair for c_x = -1, node B of the last for c_x = +1)
+// does not exist either. (Aligned half2 stores of the c_x != 0 populations, with the
+// neighbouring pair's value taken by a warp shuffle, measured slower: 2.02 against 1.85
+// ms per 512^3 AA step, for the extra shuffles and edge stores.)
+template <bool CHECK>
+__device__ __forceinline__ void push_gather_rows(const SweepArgs& a, const f32x2 (&h)[Q], const uint32_t (&zoff)[3],
+                                                 const uint32_t (&yoff)[3], uint32_t x0, uint32_t xam, uint32_t xbp,
+                                                 int fxA, int fxB, int fy, int fz) {
+  static_for<0, Q>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    if (CHECK && ((fy == 1 && cy(k) < 0) || (fy == 2 && cy(k) > 0) || (fz == 1 && cz(k) < 0) || (fz == 2 && cz(k) > 0)))
+      return;
+    const uint32_t at = zoff[1 + cz(k)] + yoff[1 + cy(k)];  // target row start + x0
+    __half* pop = static_cast<__half*>(a.dst_pop[k]);
+    if constexpr (cx(k) == 0) {
+      stg_half2(pop + chk(at, a.N - 1), h[k].x, h[k].y);
+    } else if constexpr (cx(k) > 0) {  // A -> x0 + 1, B -> x0 + 2
+      pop[chk(at + 1, a.N)] = __float2half_rn(h[k].x);
+      if (fxB != 2) pop[chk(at - x0 + xbp, a.N)] = __float2half_rn(h[k].y);
+    } else {  // A -> x0 - 1, B -> x0
+      if (fxA != 1) pop[chk(at - x0 + xam, a.N)] = __float2half_rn(h[k].x);
+      pop[chk(at, a.N)] = __float2half_rn(h[k].y);
+    }
+  });
+}
+
 // FIXED: R * nx equals ROWS_STAGE_NODES (nx 256 or 512), so the distance between the
 // population rows of a stage is a constant folded into the shared-memory load offsets
 // (measured 1.65 against 1.71 ms per 512^3 step with the distance in a register).
@@ -1361,31 +1391,18 @@ __global__ void __launch_bounds__(ROWS_THREADS, 3) sweep_rows_kernel(const __gri
       collide(h, m, f32x2(a.omegaf));
       const uint32_t cell = r * nx + x0;
       if constexpr (MODE == STREAM_AA_GATHER) {
-        // push f*_k to slot k of node x + c_k; a target beyond a walled face does not exist
+        // push f*_k to slot k of node x + c_k: the target row starts at
+        // zoff[1 + c_z] + yoff[1 + c_y]; only a pair on a walled y or z face has targets
+        // that do not exist, so only those rows test each population
         const uint32_t ym = y ? y - 1 : (py ? a.ny - 1 : 0);
         const uint32_t yp = (y + 1 < a.ny) ? y + 1 : (py ? 0 : a.ny - 1);
         const uint32_t zm = z ? z - 1 : (pz ? a.nz - 1 : 0);
         const uint32_t zp = (z + 1 < a.nz) ? z + 1 : (pz ? 0 : a.nz - 1);
-        static_for<0, Q>([&](auto kc) {
-          constexpr int k = decltype(kc)::value;
-          const bool in_yz = !((fy == 1 && cy(k) < 0) || (fy == 2 && cy(k) > 0) || (fz == 1 && cz(k) < 0) ||
-                               (fz == 2 && cz(k) > 0));
-          if (in_yz) {
-            __half* pop = static_cast<__half*>(a.dst_pop[k]);
-            const uint32_t ty = cy(k) > 0 ? yp : (cy(k) < 0 ? ym : y);
-            const uint32_t tz = cz(k) > 0 ? zp : (cz(k) < 0 ? zm : z);
-            const uint32_t trow = (tz * a.ny + ty) * nx;
-            if constexpr (cx(k) == 0) {
-              stg_half2(pop + chk(trow + x0, a.N - 1), h[k].x, h[k].y);
-            } else if constexpr (cx(k) > 0) {  // A -> x0 + 1, B -> x0 + 2
-              pop[chk(trow + x0 + 1, a.N)] = __float2half_rn(h[k].x);
-              if (fxB != 2) pop[chk(trow + xbp, a.N)] = __float2half_rn(h[k].y);
-            } else {  // A -> x0 - 1, B -> x0
-              if (fxA != 1) pop[chk(trow + xam, a.N)] = __float2half_rn(h[k].x);
-              pop[chk(trow + x0, a.N)] = __float2half_rn(h[k].y);
-            }
-          }
-        });
+        const uint32_t plane = a.ny * nx;
+        const uint32_t zoff[3] = {zm * plane, z * plane, zp * plane};
+        const uint32_t yoff[3] = {ym * nx + x0, y * nx + x0, yp * nx + x0};
+        if ((fy | fz) == 0) push_gather_rows<false>(a, h, zoff, yoff, x0, xam, xbp, fxA, fxB, 0, 0);
+        else push_gather_rows<true>(a, h, zoff, yoff, x0, xam, xbp, fxA, fxB, fy, fz);
       } else {
         static_for<0, Q>([&](auto kc) {
           constexpr int k = decltype(kc)::value;
