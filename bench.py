@@ -42,6 +42,8 @@ def workload(name: str):
         return inp.channel(512, 512, 512, 0.8, (0.04, 0.01, 0.0))
     if name == "channel256":  # the same channel at 256^3, for profiler captures
         return inp.channel(256, 256, 256, 0.8, (0.04, 0.01, 0.0))
+    if name == "channel512x64":  # 512-node rows as at 512^3, 64 planes: profiler captures
+        return inp.channel(512, 512, 64, 0.8, (0.04, 0.01, 0.0))
     if name == "duct":
         return inp.duct(256, 64, 64, 0.6, 0.05, 30.0)
     if name == "couette":
@@ -305,14 +307,14 @@ def run_variant(wl, precision, steps, warmup, resid_every, dist_ctx, clocks=None
     return out
 
 
-def e2e_run(wl, precision, steps, resid_every, dist_ctx):
+def e2e_run(wl, precision, steps, resid_every, dist_ctx, scheme="ab"):
     """Same solve through the public API with host buffers: upload the initial
     populations from pinned host memory, run the steps, read the density and velocity
     fields back to pinned host memory -- all inside the timed region."""
     import torch
 
     import paper_0811_4593_gb300 as lbm
-    with lbm.Lattice.from_workload(wl, precision) as lat:
+    with lbm.Lattice.from_workload(wl, precision, scheme=scheme) as lat:
         dt = {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16}[precision]
         mdt = torch.float64 if precision == "f64" else torch.float32
         f_host = torch.empty((19, wl.nz, wl.ny, wl.nx), dtype=dt, pin_memory=True)
@@ -387,13 +389,15 @@ def native(args):
 
     import paper_0811_4593_gb300 as lbm
     from paper_0811_4593_gb300 import build as lib_build
+    if args.sweep_scheme == "aa" and (args.steps % 2 or args.warmup % 2 or args.resid_every % 2):
+        raise SystemExit("an AA lattice advances in pairs of steps: give even --steps, --warmup and --resid-every")
     d = Dist()
     if d.rank == 0 or not os.path.exists(lib_build.LIB):
         lib_build.build()
     d.init("nccl")
     wl = workload(args.workload)
     hbm, hbm_src = measured_hbm_peak()
-    with lbm.Lattice.from_workload(wl, args.precision) as lat:
+    with lbm.Lattice.from_workload(wl, args.precision, scheme=args.sweep_scheme) as lat:
         total_ms, sweep_ms, launches, clock = measure(lat, args.steps, args.warmup, args.resid_every, d,
                                                       clock_gpu=d.local)
     total_ms = d.max(total_ms)
@@ -405,20 +409,22 @@ def native(args):
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": describe(wl), "nodes": wl.cells, "precision": f"{args.precision} population storage",
+                   "streaming": "A/B (two arrays)" if args.sweep_scheme == "ab" else "AA (one array)",
                    "residual_every": args.resid_every, "parallelism": "replicas" if d.world > 1 else "single GPU",
                    "l2": f"inputs larger than L2: {BYTES_PER_UPDATE[args.precision] * wl.cells / 2e9:.1f} GB of "
                          f"populations read per step (no flush needed)"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "peak_source": hbm_src,
-                     "traffic": profiled_traffic("sweep", args.precision, args.workload),
-                     "kernel": sweep_kernel_name(wl, args.precision),
+                     "traffic": profiled_traffic("sweep", args.precision, args.workload)
+                     if args.sweep_scheme == "ab" else None,
+                     "kernel": sweep_kernel_name(wl, args.precision, args.sweep_scheme),
                      "bytes_per_update": BYTES_PER_UPDATE[args.precision], "updates_per_launch": wl.cells,
                      "sweep_ms": round(sweep_ms, 4)},
         "gpu_launches": launches,
         "clocks": clock,
     }
     if not args.no_e2e:
-        dt_s, h2d, d2h = e2e_run(wl, args.precision, args.steps, args.resid_every, d)
+        dt_s, h2d, d2h = e2e_run(wl, args.precision, args.steps, args.resid_every, d, args.sweep_scheme)
         dt_s = d.max(dt_s)
         out["e2e"] = {"value": round(whole_job_mlups(d.world, wl.cells, args.steps, dt_s * 1e3), 1), "unit": "MLUPS",
                       "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
@@ -899,7 +905,10 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", default="channel512", choices=["channel512", "channel256", "duct", "couette"])
+    ap.add_argument("--workload", default="channel512",
+                    choices=["channel512", "channel256", "channel512x64", "duct", "couette"])
+    ap.add_argument("--sweep-scheme", choices=["ab", "aa"], default="ab",
+                    help="streaming scheme of the benchmarked lattice (AA: step pairs, so even step counts)")
     ap.add_argument("--precision", default="f32", choices=["f32", "f16", "f64"])
     ap.add_argument("--resid-every", type=int, default=100)
     ap.add_argument("--variant-steps", type=int, default=200)
