@@ -1,8 +1,9 @@
 """GPU parity on the benchmark configurations at their stated sizes: the 256 x 64 x 64
-square duct (tilted parabolic inlet and outlet, resting walls, tau 0.6 and 1.0) and the
-plane Poiseuille sweep (4 x 4 x Lz, parabolic inlet and outlet of peak 0.02), each run
-from rest for a few hundred to a few thousand steps on the GPU and in the FP64 oracle,
-compared node by node (velocity error in units of the largest velocity).
+square duct (tilted parabolic inlet and outlet, resting walls, tau 0.6 and 1.0; at tau
+0.6 also in one array with AA streaming) and the plane Poiseuille sweep (4 x 4 x Lz,
+parabolic inlet and outlet of peak 0.02), each run from rest for a few hundred to a few
+thousand steps on the GPU and in the FP64 oracle, compared node by node (velocity error
+in units of the largest velocity).
 
 Bars: FP64 1e-12, FP32 1e-5; binary16 storage at about twice the error measured for
 each case on a GB300 (duct 5.2e-4 / 4.4e-4 at tau 0.6 / 1.0; Poiseuille 4.2e-4, 2.9e-4,
@@ -32,13 +33,13 @@ def cuda():
     torch.cuda.set_device(0)
 
 
-def gpu_and_oracle(wl, prec, steps):
+def gpu_and_oracle(wl, prec, steps, scheme="ab"):
     import oracle
     import paper_0811_4593_gb300 as lbm
     olat = oracle.Lattice.from_workload(wl)
     ref = oracle.run(olat, oracle.init_equilibrium(olat), steps)
     _, uo = oracle.macros(olat, ref)
-    with lbm.Lattice.from_workload(wl, prec) as lat:
+    with lbm.Lattice.from_workload(wl, prec, scheme=scheme) as lat:
         lat.step(steps)
         _, u = lat.macros()
         u = u.double().cpu().numpy()
@@ -51,6 +52,16 @@ def test_duct_256x64x64_against_oracle(prec, tau):
     err = gpu_and_oracle(inp.duct(256, 64, 64, tau, 0.05, 30.0), prec, 300)
     print(f"duct tau {tau} {prec}: {err:.3e}")
     assert err <= (F16_TOL[("duct", tau)] if prec == "f16" else TOL[prec]), err
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_duct_256x64x64_aa_against_oracle(prec):
+    """The same duct in one array (AA streaming): the binary16 lattice runs the row-staged
+    AA steps (256-node rows), whose pushes test each population for a target beyond the
+    walled y and z faces on the wall rows."""
+    err = gpu_and_oracle(inp.duct(256, 64, 64, 0.6, 0.05, 30.0), prec, 300, scheme="aa")
+    print(f"duct AA tau 0.6 {prec}: {err:.3e}")
+    assert err <= (F16_TOL[("duct", 0.6)] if prec == "f16" else TOL[prec]), err
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
