@@ -80,11 +80,39 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def code_only(text: str) -> str:
+    """C/C++/CUDA source with its comments, blank lines and the blanks around each line
+    removed, so that the hash of the sweep source changes with the code and not with
+    its comments or indentation. String and character literals are kept as they are."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = [ln.strip() for ln in "".join(out).splitlines()]
+    return "\n".join(ln for ln in lines if ln)
+
+
 def sweep_source_hash() -> str:
+    """Hash of the sweep's code (kernels.cuh, d3q19.cuh; comments excluded): a profiled
+    traffic figure is reported only while this matches the hash it was captured on."""
     h = hashlib.sha256()
     for f in ("kernels.cuh", "d3q19.cuh"):
-        with open(os.path.join(ROOT, "paper_0811_4593_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_0811_4593_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

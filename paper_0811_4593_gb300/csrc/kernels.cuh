@@ -1136,10 +1136,11 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) sweep_pair_kernel(const __gr
 // destination rows (y, z). One producer warp issues, per row, the 19 bulk copies
 // (cp.async.bulk, global -> shared, completing on the stage's "full" mbarrier) of the
 // source rows the pull reads -- population k of row (y - c_ky, z - c_kz) -- into a ring
-// of ROWS_STAGES shared-memory stages; eight consumer warps wait on a stage, compute
-// its row and release the stage on its "empty" mbarrier, so the two sides run
-// decoupled, without block-wide barriers. The x shift of the pull is an index into the
-// staged row. Whole rows in flight in shared memory replace loads held in registers,
+// of ROWS_STAGES shared-memory stages; eight consumer warps wait on a stage, read
+// their pairs' populations from it and release it at once on its "empty" mbarrier (one
+// arrival per consumer thread), then compute and store while the producer refills it:
+// the two sides run decoupled, without block-wide barriers. The x shift of the pull is
+// an index into the staged row. Whole rows in flight in shared memory replace loads held in registers,
 // which bounded the register-staged paired sweep (64 registers, 32 warps per SM,
 // latency-bound). Consumers compute node pairs (x0, x0 + 1) with the paired sweep's
 // per-node code (same closure, packed moments and collision), so the bits are those

@@ -43,6 +43,17 @@ def test_traffic_is_reported_only_for_the_profiled_source(monkeypatch):
     assert bench.profiled_traffic("sweep", "f32", "no_such_workload") is None
 
 
+def test_code_hash_ignores_comments_and_keeps_literals():
+    src = 'int a = 1; // one\n/* block\n comment */ asm("add.f32 %0, %1; // not a comment" : "=f"(x));\n'
+    same = 'int a = 1;   // another note\nasm("add.f32 %0, %1; // not a comment" : "=f"(x));\n'
+    changed = 'int a = 2;\nasm("add.f32 %0, %1; // not a comment" : "=f"(x));\n'
+    code = bench.code_only(src)
+    assert "one" not in code and "block" not in code and "// not a comment" in code
+    assert bench.code_only(same) == code
+    assert bench.code_only(changed) != code
+    assert bench.code_only("char c = '\\''; // x\n") == "char c = '\\'';"
+
+
 class _FakeSmi:
     def __init__(self, text):
         self.text = text
