@@ -43,6 +43,16 @@ def test_traffic_is_reported_only_for_the_profiled_source(monkeypatch):
     assert bench.profiled_traffic("sweep", "f32", "no_such_workload") is None
 
 
+@pytest.mark.parametrize("steps,warmup,every", [(11, 4, 100), (10, 3, 100), (10, 4, 5)])
+def test_aa_sweep_wants_step_pairs(steps, warmup, every):
+    class A:
+        sweep_scheme = "aa"
+
+    A.steps, A.warmup, A.resid_every = steps, warmup, every
+    with pytest.raises(SystemExit, match="pairs of steps"):
+        bench.native(A())
+
+
 def test_code_hash_ignores_comments_and_keeps_literals():
     src = 'int a = 1; // one\n/* block\n comment */ asm("add.f32 %0, %1; // not a comment" : "=f"(x));\n'
     same = 'int a = 1;   // another note\nasm("add.f32 %0, %1; // not a comment" : "=f"(x));\n'
