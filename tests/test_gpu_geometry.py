@@ -104,7 +104,7 @@ def test_corner_codes_equal_box_corners_bitwise(prec):
         np.testing.assert_array_equal(b.get_populations()[:, 1:-1, 1:-1, 1:-1], a.get_populations())
 
 
-# FP32 bars: the benchmark spec's 1e-5 at the paper's tau = 2 (measured 9.1e-6 with the
+# FP32 bars: the FP32 velocity bar of 1e-5 at the paper's tau = 2 (measured 9.1e-6 with the
 # compensated moment sums of the geometry/force sweep); at tau = 1 float storage alone
 # (FP64 arithmetic on a state rounded to shifted float every step) leaves 1.1e-5 in this
 # steady flow, and the float sweep measures 2.0e-5, so its bar is 2.5e-5
